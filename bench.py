@@ -1,0 +1,423 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 SpTRSV with equation rewriting.
+
+Metric: effective bandwidth of one solve, GB/s = B_alg / t_solve, where
+B_alg = 12 nnz + 4 (n+1) + 16 n nrhs are the algorithmic bytes of the plain
+problem (FP64 values + int32 columns, row pointers, b read, x written), the
+same for the plain and the rewritten solve, so GB/s ratios are speed-ups.
+
+Workload: lower triangle of the 3D 7-point Laplacian on a 128^3 grid
+(n = 2,097,152, nnz = 8,339,456, 382 levels), diagonal 6 + U[0, 0.1], one
+right-hand side b ~ U[-1, 1]; synthetic, seeded.  A step is one solve of the
+rewritten, autotuned plan (analysis and transform are one-time set-up, timed
+and reported apart).  The plain level-set solve of the same matrix is timed
+the same way and reported beside it.
+
+`--impl reference` times the CPU oracle (serial FP64 forward substitution)
+on the same workload, each step one full solve.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "stencil3d_128"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def b_alg(n: int, nnz: int, nrhs: int = 1) -> int:
+    return 12 * nnz + 4 * (n + 1) + 16 * n * nrhs
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--side", type=int, default=128, help="grid side of the 3D stencil")
+    ap.add_argument("--depths", default="1,2,3,4,6",
+                    help="fixed rewrite depths tried besides heuristic H")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def workload(side: int):
+    import matgen as mg
+    A = mg.stencil3d(side, seed=2000)
+    b = mg.rhs_uniform(A.n, seed=2001)
+    return A, b
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def solve_source_digest() -> str:
+    h = hashlib.sha256()
+    for f in ("solve.cu", "solve.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2103_11445_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_tag: str):
+    """Per-launch DRAM bytes of the timed kernel from the committed ncu
+    summary, if that summary was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}_{WORKLOAD}.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_digest") != solve_source_digest():
+        return None
+    try:
+        return int(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.split(", ") for r in self.tmp.read().strip().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        if self.uuid:
+            mine = [r for r in rows if len(r) > 1 and self.uuid in r[1]]
+            rows = mine or rows
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[2]))
+                smax.append(float(r[3]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[6:10]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+
+def oracle_solve_timed(A, b, seconds: float, min_runs: int = 3, max_runs: int = 1000):
+    import oracle
+    times, x = [], None
+    t_start = time.perf_counter()
+    while len(times) < max_runs:
+        t0 = time.perf_counter()
+        x = oracle.forward_subst(A, b)
+        times.append(time.perf_counter() - t0)
+        if len(times) >= min_runs and time.perf_counter() - t_start >= seconds:
+            break
+    return x, times
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    A, b = workload(args.side)
+    import oracle
+    oracle.build()
+    for _ in range(max(args.warmup, 0)):
+        oracle.forward_subst(A, b)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.forward_subst(A, b)
+        times.append(time.perf_counter() - t0)
+    B = b_alg(A.n, A.nnz)
+    ms = statistics.median(times) * 1e3
+    val = B / (ms * 1e-3) / 1e9
+    line = {
+        "impl": "reference", "metric": "SpTRSV eff. GB/s (B_alg / t_solve), FP64",
+        "value": round(val, 4), "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"stencil3d_{args.side} (3D 7-point lower triangle, n={A.n}, "
+                               f"nnz={A.nnz}, 1 RHS)", "b_alg_bytes": B},
+        "cpu_baseline": {"value": round(val, 4), "unit": "GB/s", "cores": 1,
+                         "kind": "oracle",
+                         "sample": f"{args.steps} full serial FP64 forward substitutions "
+                                   f"(median), C oracle, 1 thread of "
+                                   f"{len(os.sched_getaffinity(0))} available"},
+        "e2e": {"value": round(val, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_2103_11445_gb300 import binding as Bd
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    A, b_np = workload(args.side)
+    n, nnz = A.n, A.nnz
+    B = b_alg(n, nnz)
+    rp = torch.as_tensor(A.row_ptr, device=dev)
+    col = torch.as_tensor(A.col, device=dev)
+    val = torch.as_tensor(A.val, device=dev)
+    b = torch.as_tensor(b_np, device=dev)
+    x = torch.empty_like(b)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P = Bd.Plan(n, rp, col, val)
+    torch.cuda.synchronize()
+    analyze_ms = (time.perf_counter() - t0) * 1e3
+    nlev = P.info()["nlev"]
+
+    def timed(nsolves: int, warm: int = 2, profile=False):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(nsolves)]
+        for _ in range(warm):
+            flush.zero_()
+            P.solve(b, x)
+        kern = []
+        if profile:
+            Bd.sptrsv_set_profiling(P.handle, True)
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            P.solve(b, x)
+            e1.record(stream)
+            if profile:
+                kern.append(Bd.sptrsv_last_kernel_ms(P.handle))
+        torch.cuda.synchronize()
+        if profile:
+            Bd.sptrsv_set_profiling(P.handle, False)
+        P.check()
+        return [a.elapsed_time(c) for a, c in ev], kern
+
+    # candidates: plain level sets, heuristic H, fixed depths; each autotuned
+    cands = [("plain", dict(select_mode=Bd.SELECT_NONE)),
+             ("heuristic", dict(select_mode=Bd.SELECT_HEURISTIC))]
+    for d in [int(v) for v in args.depths.split(",") if v.strip()]:
+        cands.append((f"fixed_d{d}", dict(select_mode=Bd.SELECT_FIXED, depth=d)))
+    results = {}
+    for name, kw in cands:
+        t0 = time.perf_counter()
+        P.transform(solve_mode=Bd.SOLVE_AUTO, **kw)
+        tr_ms = (time.perf_counter() - t0) * 1e3
+        ts, _ = timed(5)
+        info = P.info()
+        results[name] = dict(ms=statistics.median(ts), transform_ms=tr_ms, kw=kw,
+                             nlev_new=info["nlev_new"], flops_new=info["flops_new"],
+                             solve_mode=info["solve_mode"], L=info["lanes_per_row"],
+                             block=info["block_threads"], grid=info["grid_blocks"],
+                             cta_run_rows=info["cta_run_rows"])
+    rewritten = {k: v for k, v in results.items() if k != "plain"}
+    best = min(rewritten, key=lambda k: rewritten[k]["ms"])
+
+    def measure(kw, steps, warmup, label):
+        P.transform(solve_mode=Bd.SOLVE_AUTO, **kw)
+        info = P.info()
+        barrier(world)
+        torch.cuda.synchronize()
+        step_ms, kern_ms = timed(steps, warm=warmup, profile=True)
+        barrier(world)
+        return info, step_ms, kern_ms
+
+    # plain level-set, same protocol
+    pinfo, p_steps, p_kern = measure(results["plain"]["kw"], args.steps, args.warmup, "plain")
+    plain_ms = max_over_ranks(world, statistics.mean(p_steps))
+
+    # headline: rewritten, autotuned
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    info, steps_ms, kern_ms = measure(rewritten[best]["kw"], args.steps, args.warmup, best)
+    clk = clocks.stop()
+    ms = max_over_ranks(world, statistics.mean(steps_ms))
+    value = B * world / (ms * 1e-3) / 1e9
+    kern_mean = statistics.mean(kern_ms)
+    peak, peak_kind = peaks()
+    achieved = B / (kern_mean * 1e-3) / 1e9
+    kernel_tag = "solve_syncfree" if info["solve_mode"] == Bd.SOLVE_SYNCFREE else "solve_barrier"
+
+    # end to end through the public API: pinned host b in, host x out
+    b_host = torch.from_numpy(b_np.copy()).pin_memory()
+    x_host = torch.empty_like(b_host).pin_memory()
+    bd = torch.empty_like(b)
+    xd = torch.empty_like(b)
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bd.copy_(b_host, non_blocking=True)
+        P.solve(bd, xd)
+        x_host.copy_(xd, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    P.check()
+    e2e_val = B * world / (max_over_ranks(world, statistics.mean(e2e_ms)) * 1e-3) / 1e9
+    launches_per_solve = 2 if info["solve_mode"] == Bd.SOLVE_SYNCFREE else 1
+
+    line = {
+        "metric": "SpTRSV eff. GB/s (B_alg / t_solve), rewritten + autotuned, FP64",
+        "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {
+            "workload": f"stencil3d_{args.side} (3D 7-point Laplacian lower triangle, n={n}, "
+                        f"nnz={nnz}, diag 6+U[0,0.1], 1 RHS b~U[-1,1])",
+            "b_alg_bytes": B, "levels": nlev, "levels_after": info["nlev_new"],
+            "selection": best, "solve_mode": "syncfree" if launches_per_solve == 2 else "barrier",
+            "lanes_per_row": info["lanes_per_row"], "block_threads": info["block_threads"],
+            "grid_blocks": info["grid_blocks"], "cta_run_rows": info["cta_run_rows"],
+            "flops_plain": info["flops_plain"], "flops_rewritten": info["flops_new"],
+            "l2": "flushed before every step (256 MiB write, outside the events)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "analyze_ms": round(analyze_ms, 2),
+            "transform_ms": round(rewritten[best]["transform_ms"], 2),
+        },
+        "plain_levelset": {
+            "value": round(B * world / (plain_ms * 1e-3) / 1e9, 3), "unit": "GB/s",
+            "ms_per_step": round(plain_ms, 5),
+            "solve_mode": "syncfree" if pinfo["solve_mode"] == Bd.SOLVE_SYNCFREE else "barrier",
+            "lanes_per_row": pinfo["lanes_per_row"], "cta_run_rows": pinfo["cta_run_rows"],
+        },
+        "speedup_vs_plain": round(plain_ms / ms, 3),
+        "candidates": {k: {"ms": round(v["ms"], 4), "levels": v["nlev_new"],
+                           "flops": v["flops_new"],
+                           "mode": "syncfree" if v["solve_mode"] == 2 else "barrier",
+                           "L": v["L"], "cta_run_rows": v["cta_run_rows"]}
+                       for k, v in results.items()},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "peak_kind": f"{peak_kind} copy bandwidth",
+                     "kernel": f"{kernel_tag} (mean of {len(kern_ms)} launches, "
+                               f"{kern_mean * 1e3:.1f} us, CUDA events on the launch stream)",
+                     "traffic": profiled_traffic(kernel_tag)},
+        "e2e": {"value": round(e2e_val, 3), "unit": "GB/s", "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": launches_per_solve * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1:
+        x_gpu = x.cpu().numpy()
+        x_ref, ts = oracle_solve_timed(A, b_np, args.cpu_seconds)
+        import oracle
+        cpu_ms = statistics.median(ts) * 1e3
+        line["cpu_baseline"] = {
+            "value": round(B / (cpu_ms * 1e-3) / 1e9, 4), "unit": "GB/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{len(ts)} full serial FP64 forward substitutions of the same matrix "
+                      f"(median {cpu_ms:.1f} ms), C oracle, 1 of "
+                      f"{len(os.sched_getaffinity(0))} host cores"}
+        line["relerr_vs_oracle"] = oracle.relerr(x_gpu, x_ref)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        rc = run_reference(args, world, rank)
+    else:
+        rc = run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

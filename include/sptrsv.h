@@ -1,0 +1,214 @@
+/*
+ * sptrsv.h -- C ABI of the GB300 sparse lower-triangular solver with
+ * equation rewriting (Yilmaz, "Graph Transformation and Specialized Code
+ * Generation for Sparse Triangular Solve (SpTRSV)", arXiv:2103.11445).
+ *
+ * The problem (Sec. II): solve L x = b for a sparse lower-triangular L stored
+ * in CSR (Fig. 1).  Rows are grouped into levels of the dependency graph
+ * DAG_L; levels run one after another.  Sec. III rewrites the equations of
+ * rows in thin levels by substituting the equations of their dependencies,
+ * which lifts those rows into earlier levels and removes levels (and the
+ * synchronisation at their ends).  Rearranged back into L x = b form
+ * (Fig. 3) a rewritten row keeps its diagonal, depends on fewer and earlier
+ * unknowns, and carries a right-hand side  b_i - sum_j c_j b_j.
+ *
+ * Conventions that hold for every call:
+ *  - Pointers prefixed d_ are device pointers of the current CUDA device,
+ *    h_ are host pointers.  All caller buffers stay owned by the caller; the
+ *    library never frees them and keeps no reference after a call returns.
+ *  - CSR: row_ptr int32[n+1] (row_ptr[0] == 0, non-decreasing), col
+ *    int32[nnz] strictly ascending inside each row, every column <= its row,
+ *    the diagonal stored (as the last entry of the row) and non-zero.
+ *    Values are FP64.  Every stored off-diagonal entry is a dependency, even
+ *    an explicit 0.0.
+ *  - Right-hand sides and solutions are row-major [n][nrhs], contiguous
+ *    (the layout of a C-contiguous torch tensor of shape (n, nrhs)).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  sptrsv_solve and sptrsv_batch_solve are asynchronous with
+ *    respect to the host; sptrsv_analyze and sptrsv_transform synchronise
+ *    the stream because the host needs level counts to plan.
+ *  - Errors the host can see are returned at once.  Errors a kernel finds
+ *    (invalid CSR, a bounded wait that ran out) are latched in the plan and
+ *    returned by the next sptrsv_check (which synchronises) or by the next
+ *    synchronising call.  A plan with a latched error refuses further work
+ *    with SPTRSV_ERR_BAD_STATE until it is destroyed.
+ *  - A plan is used by one host thread at a time; solves on one plan must not
+ *    overlap on the device (they share the plan's scratch).
+ */
+#ifndef SPTRSV_H
+#define SPTRSV_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SPTRSV_API __attribute__((visibility("default")))
+#else
+#define SPTRSV_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPTRSV_OK = 0,
+    SPTRSV_ERR_INVALID_ARG = 1,   /* null pointer, negative size, x aliases b */
+    SPTRSV_ERR_NOT_LOWER = 2,     /* a column above the diagonal or out of range */
+    SPTRSV_ERR_UNSORTED = 3,      /* columns of a row not strictly ascending,
+                                     or row_ptr not non-decreasing */
+    SPTRSV_ERR_ZERO_DIAG = 4,
+    SPTRSV_ERR_MISSING_DIAG = 5,
+    SPTRSV_ERR_OOM = 6,           /* device allocation failed */
+    SPTRSV_ERR_CUDA = 7,          /* a CUDA runtime call failed */
+    SPTRSV_ERR_TIMEOUT = 8,       /* a bounded device wait gave up */
+    SPTRSV_ERR_BAD_STATE = 9,     /* call out of order or plan already failed */
+    SPTRSV_ERR_UNSUPPORTED = 10   /* size or mode this build does not handle */
+} sptrsv_status_t;
+
+typedef struct sptrsv_plan_s *sptrsv_plan_t;    /* opaque, owned by the library */
+typedef struct sptrsv_batch_s *sptrsv_batch_t;  /* opaque, owned by the library */
+typedef struct sptrsv_mlp_s *sptrsv_mlp_t;      /* opaque, owned by the library */
+typedef void *sptrsv_stream_t;                  /* cudaStream_t */
+
+/* Row selection for the rewriting (Sec. III; the paper chooses rows by
+ * hand, Sec. IV). */
+enum {
+    SPTRSV_SELECT_NONE = 0,       /* plain level sets, nothing rewritten */
+    SPTRSV_SELECT_HEURISTIC = 1,  /* thin-level heuristic H (below) */
+    SPTRSV_SELECT_COSTMODEL = 2,  /* learned cost model picks the depth per
+                                     segment; needs sptrsv_set_costmodel */
+    SPTRSV_SELECT_FIXED = 3       /* merge every `depth`+1 consecutive levels */
+};
+enum { SPTRSV_SOLVE_AUTO = 0, SPTRSV_SOLVE_BARRIER = 1, SPTRSV_SOLVE_SYNCFREE = 2 };
+enum { SPTRSV_F64 = 0, SPTRSV_F32_IR = 1 };
+
+/* Parameters of sptrsv_transform.  Fill with sptrsv_default_params first.
+ *
+ * Heuristic H: levels are scanned in order; each new level starts at a kept
+ * level t and absorbs the following levels t+1, t+2, ... (their rows are
+ * rewritten to depend only on levels < t) while the next level has fewer
+ * than `thin_rows` rows, at most `max_depth` levels have been absorbed, no
+ * rewritten row would exceed `max_row_fill` off-diagonal terms, and the FLOPs
+ * added over the whole matrix stay <= flop_budget * FLOPs of the plain solve
+ * (FLOPs: 2 per off-diagonal term, x or b, plus 1 per row). */
+typedef struct {
+    int32_t select_mode;     /* SPTRSV_SELECT_* (default HEURISTIC) */
+    int32_t depth;           /* FIXED mode: levels absorbed per new level */
+    int32_t thin_rows;       /* tau; <= 0: number of resident warps / 4 */
+    int32_t max_depth;       /* d_max, 0..16 (default 8) */
+    double flop_budget;      /* rho; < 0: 0.10 (the +10% of Sec. V) */
+    int32_t max_row_fill;    /* cap on off-diagonal terms of a rewritten row
+                                (default 1024, at most 4096) */
+    int32_t solve_mode;      /* SPTRSV_SOLVE_* (default AUTO = autotune) */
+    int32_t precision;       /* SPTRSV_F64 or SPTRSV_F32_IR */
+    double ir_tol;           /* F32_IR: stop when |b - L x|_inf <=
+                                ir_tol * (|L|_inf |x|_inf + |b|_inf); default 1e-15 */
+    int32_t ir_max_iter;     /* F32_IR: refinement steps at most (default 8,
+                                0 = plain FP32 solve, < 0 = default, max 64) */
+    int32_t lanes_per_row;   /* 1,2,4,8,16,32; 0 = auto */
+    int32_t block_threads;   /* 128..1024, multiple of 32; 0 = auto */
+    int32_t cta_run_rows;    /* levels of at most this many rows run inside
+                                one CTA (no grid barrier); 0 = auto, <0 = off */
+    int32_t wait_timeout_ms; /* bound on every device wait (default 5000); a
+                                solve longer than this is reported as TIMEOUT */
+} sptrsv_transform_params_t;
+
+/* Everything a caller may want to report about a plan. */
+typedef struct {
+    int32_t n;
+    int64_t nnz;
+    int32_t nlev;            /* levels of DAG_L */
+    int32_t nlev_new;        /* levels solved after the transform */
+    int32_t rows_rewritten;
+    int64_t nnz_x;           /* off-diagonal x terms in the solve structure */
+    int64_t nnz_b;           /* b terms of rewritten rows */
+    int64_t flops_plain;     /* per right-hand side: 2 (nnz - n) + n */
+    int64_t flops_new;       /* 2 (nnz_x + nnz_b) + n */
+    int32_t select_mode, solve_mode, precision;
+    int32_t lanes_per_row, block_threads, grid_blocks, cta_run_rows;
+    int32_t thin_rows, max_depth;
+    double flop_budget;
+    int32_t ir_iters_last;   /* refinement steps of the last F32_IR solve
+                                (valid after a synchronisation) */
+    int32_t num_sms;
+    double analyze_ms, transform_ms;
+} sptrsv_info_t;
+
+SPTRSV_API const char *sptrsv_status_string(sptrsv_status_t s);
+SPTRSV_API void sptrsv_default_params(sptrsv_transform_params_t *prm);
+
+/* Level analysis of DAG_L (Sec. II; level sets as in Sec. II's related
+ * work, built here on the device by validation, a transpose and a parallel
+ * breadth-first traversal of the DAG, Sec. IV's matrix-analysis module).
+ * Copies the CSR into the plan, so the caller may free it afterwards.
+ * Returns the validation error codes above for malformed CSR.  On success
+ * *out is a plan that solves the plain level sets. */
+SPTRSV_API sptrsv_status_t sptrsv_analyze(int32_t n, int64_t nnz, const int32_t *d_row_ptr,
+                               const int32_t *d_col, const double *d_val,
+                               sptrsv_stream_t stream, sptrsv_plan_t *out);
+
+/* Equation rewriting (Sec. III, Figs. 2-3): select rows (prm->select_mode),
+ * compute on the device the fill of every candidate rewrite, the rewritten
+ * coefficients and right-hand-side weights (FP64 always), assemble the
+ * level-ordered solve structure and, for SPTRSV_SOLVE_AUTO, time candidate
+ * launch configurations on it.  May be called again with other parameters;
+ * SELECT_NONE restores the plain level sets. */
+SPTRSV_API sptrsv_status_t sptrsv_transform(sptrsv_plan_t p, const sptrsv_transform_params_t *prm,
+                                 sptrsv_stream_t stream);
+
+/* x = L^{-1} b for nrhs right-hand sides (1..32 per launch; more are solved
+ * 32 columns at a time), row-major [n][nrhs] device buffers.  x must not
+ * overlap b.  Asynchronous.  In F32_IR precision the solve runs on FP32 copies
+ * of the values and refines with FP64 residuals of the original L. */
+SPTRSV_API sptrsv_status_t sptrsv_solve(sptrsv_plan_t p, const double *d_b, double *d_x,
+                             int32_t nrhs, sptrsv_stream_t stream);
+
+/* Synchronise `stream` and return the error latched by a kernel, if any. */
+SPTRSV_API sptrsv_status_t sptrsv_check(sptrsv_plan_t p, sptrsv_stream_t stream);
+
+SPTRSV_API sptrsv_status_t sptrsv_get_info(sptrsv_plan_t p, sptrsv_info_t *out);
+SPTRSV_API void sptrsv_plan_destroy(sptrsv_plan_t p);
+
+/* Analysis results (for inspection and tests), copied to device buffers:
+ * level int32[n], level_ptr int32[nlev+1], perm int32[n] (rows ordered by
+ * level, ascending row index inside a level).  Any pointer may be NULL. */
+SPTRSV_API sptrsv_status_t sptrsv_get_levels(sptrsv_plan_t p, int32_t *d_level,
+                                  int32_t *d_level_ptr, int32_t *d_perm,
+                                  sptrsv_stream_t stream);
+
+/* The new levels chosen by the last transform as host arrays of
+ * nlev_new entries: first original level t and number of absorbed levels d
+ * (levels t..t+d form one new level). */
+SPTRSV_API sptrsv_status_t sptrsv_get_segments(sptrsv_plan_t p, int32_t *h_first,
+                                    int32_t *h_depth);
+
+/* The transformed system in original row order (for inspection and tests).
+ * Row i: x_i = (b_i - sum bw * b[bcol] - sum xval * x[xcol]) / diag_i.
+ * Sizes: new_level int32[n], xptr/bptr int64[n+1], xcol/xval [nnz_x],
+ * bcol/bw [nnz_b] (sptrsv_info_t).  Columns ascending inside a row. */
+SPTRSV_API sptrsv_status_t sptrsv_get_transformed(sptrsv_plan_t p, int32_t *d_new_level,
+                                       int64_t *d_xptr, int32_t *d_xcol,
+                                       double *d_xval, int64_t *d_bptr,
+                                       int32_t *d_bcol, double *d_bw,
+                                       sptrsv_stream_t stream);
+
+/* Profiling (not part of the paper's method): while enabled, sptrsv_solve
+ * records CUDA events on its stream around its main solve kernel(s) (after
+ * the sentinel pre-fill of the synchronisation-free variant; FP64 only).
+ * sptrsv_last_kernel_ms waits for the last solve's end event and returns the
+ * elapsed milliseconds; SPTRSV_ERR_BAD_STATE if no profiled solve ran. */
+SPTRSV_API sptrsv_status_t sptrsv_set_profiling(sptrsv_plan_t p, int32_t on);
+SPTRSV_API sptrsv_status_t sptrsv_last_kernel_ms(sptrsv_plan_t p, float *ms);
+
+/* Test hook for failure detection (not part of the paper's method): makes
+ * row `row` of the current solve structure read its own unknown, a wait no
+ * write can ever satisfy.  A later synchronisation-free solve must then give
+ * up after wait_timeout_ms and sptrsv_check must return SPTRSV_ERR_TIMEOUT;
+ * the plan is unusable afterwards.  The row must have at least one
+ * off-diagonal term (SPTRSV_ERR_UNSUPPORTED otherwise). */
+SPTRSV_API sptrsv_status_t sptrsv_debug_inject_wait(sptrsv_plan_t p, int32_t row);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPTRSV_H */

@@ -1,0 +1,307 @@
+"""Thin ctypes binding of ``include/sptrsv.h``.
+
+The functions here carry the C entry points' names and only marshal
+arguments: integers, raw device pointers (``tensor.data_ptr()``) and CUDA
+stream handles (``torch.cuda.Stream.cuda_stream``).  Every step of the solver
+runs in the CUDA library; if the library cannot be loaded this module raises
+instead of falling back to anything else.
+
+``Plan`` is a convenience wrapper that takes torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from ctypes import (POINTER, Structure, byref, c_char_p, c_double, c_int32,
+                    c_int64, c_void_p)
+
+from . import _build
+
+SPTRSV_OK = 0
+STATUS_NAMES = {
+    0: "OK", 1: "INVALID_ARG", 2: "NOT_LOWER", 3: "UNSORTED", 4: "ZERO_DIAG",
+    5: "MISSING_DIAG", 6: "OOM", 7: "CUDA", 8: "TIMEOUT", 9: "BAD_STATE",
+    10: "UNSUPPORTED",
+}
+SELECT_NONE, SELECT_HEURISTIC, SELECT_COSTMODEL, SELECT_FIXED = 0, 1, 2, 3
+SOLVE_AUTO, SOLVE_BARRIER, SOLVE_SYNCFREE = 0, 1, 2
+F64, F32_IR = 0, 1
+
+
+class SptrsvError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        self.name = STATUS_NAMES.get(code, str(code))
+        super().__init__(f"{what}: SPTRSV_ERR_{self.name} ({_status_string(code)})")
+
+
+class TransformParams(Structure):
+    _fields_ = [
+        ("select_mode", c_int32), ("depth", c_int32), ("thin_rows", c_int32),
+        ("max_depth", c_int32), ("flop_budget", c_double),
+        ("max_row_fill", c_int32), ("solve_mode", c_int32),
+        ("precision", c_int32), ("ir_tol", c_double), ("ir_max_iter", c_int32),
+        ("lanes_per_row", c_int32), ("block_threads", c_int32),
+        ("cta_run_rows", c_int32), ("wait_timeout_ms", c_int32),
+    ]
+
+
+class Info(Structure):
+    _fields_ = [
+        ("n", c_int32), ("nnz", c_int64), ("nlev", c_int32), ("nlev_new", c_int32),
+        ("rows_rewritten", c_int32), ("nnz_x", c_int64), ("nnz_b", c_int64),
+        ("flops_plain", c_int64), ("flops_new", c_int64),
+        ("select_mode", c_int32), ("solve_mode", c_int32), ("precision", c_int32),
+        ("lanes_per_row", c_int32), ("block_threads", c_int32),
+        ("grid_blocks", c_int32), ("cta_run_rows", c_int32),
+        ("thin_rows", c_int32), ("max_depth", c_int32), ("flop_budget", c_double),
+        ("ir_iters_last", c_int32), ("num_sms", c_int32),
+        ("analyze_ms", c_double), ("transform_ms", c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "sptrsv_status_string": (c_char_p, [c_int32]),
+    "sptrsv_default_params": (None, [POINTER(TransformParams)]),
+    "sptrsv_analyze": (c_int32, [c_int32, c_int64, c_void_p, c_void_p, c_void_p,
+                                 c_void_p, POINTER(c_void_p)]),
+    "sptrsv_transform": (c_int32, [c_void_p, POINTER(TransformParams), c_void_p]),
+    "sptrsv_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
+    "sptrsv_check": (c_int32, [c_void_p, c_void_p]),
+    "sptrsv_get_info": (c_int32, [c_void_p, POINTER(Info)]),
+    "sptrsv_plan_destroy": (None, [c_void_p]),
+    "sptrsv_get_levels": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sptrsv_get_segments": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "sptrsv_get_transformed": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p,
+                                         c_void_p, c_void_p, c_void_p, c_void_p,
+                                         c_void_p]),
+    "sptrsv_debug_inject_wait": (c_int32, [c_void_p, c_int32]),
+    "sptrsv_set_profiling": (c_int32, [c_void_p, c_int32]),
+    "sptrsv_last_kernel_ms": (c_int32, [c_void_p, POINTER(ctypes.c_float)]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libsptrsv.so (building it from source if needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"the sptrsv CUDA library is missing ({path}); "
+                               "build it with paper_2103_11445_gb300._build.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            if hasattr(lib, name):
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _status_string(code: int) -> str:
+    try:
+        return load().sptrsv_status_string(code).decode()
+    except Exception:  # pragma: no cover - only while the library is absent
+        return STATUS_NAMES.get(code, "?")
+
+
+def _check(code: int, what: str) -> None:
+    if code != SPTRSV_OK:
+        raise SptrsvError(code, what)
+
+
+# --- C entry points, same names -------------------------------------------
+
+def sptrsv_default_params() -> TransformParams:
+    prm = TransformParams()
+    load().sptrsv_default_params(byref(prm))
+    return prm
+
+
+def sptrsv_analyze(n: int, nnz: int, d_row_ptr: int, d_col: int, d_val: int,
+                   stream: int = 0) -> int:
+    out = c_void_p()
+    _check(load().sptrsv_analyze(n, nnz, d_row_ptr, d_col, d_val, stream, byref(out)),
+           "sptrsv_analyze")
+    return out.value
+
+
+def sptrsv_transform(plan: int, prm: TransformParams, stream: int = 0) -> None:
+    _check(load().sptrsv_transform(plan, byref(prm), stream), "sptrsv_transform")
+
+
+def sptrsv_solve(plan: int, d_b: int, d_x: int, nrhs: int, stream: int = 0) -> None:
+    _check(load().sptrsv_solve(plan, d_b, d_x, nrhs, stream), "sptrsv_solve")
+
+
+def sptrsv_check(plan: int, stream: int = 0) -> int:
+    return int(load().sptrsv_check(plan, stream))
+
+
+def sptrsv_get_info(plan: int) -> Info:
+    info = Info()
+    _check(load().sptrsv_get_info(plan, byref(info)), "sptrsv_get_info")
+    return info
+
+
+def sptrsv_plan_destroy(plan: int) -> None:
+    if plan:
+        load().sptrsv_plan_destroy(plan)
+
+
+def sptrsv_get_levels(plan: int, d_level: int, d_level_ptr: int, d_perm: int,
+                      stream: int = 0) -> None:
+    _check(load().sptrsv_get_levels(plan, d_level, d_level_ptr, d_perm, stream),
+           "sptrsv_get_levels")
+
+
+def sptrsv_get_segments(plan: int, nseg: int):
+    first = (c_int32 * max(nseg, 1))()
+    depth = (c_int32 * max(nseg, 1))()
+    _check(load().sptrsv_get_segments(plan, first, depth), "sptrsv_get_segments")
+    return list(first)[:nseg], list(depth)[:nseg]
+
+
+def sptrsv_get_transformed(plan: int, d_new_level: int, d_xptr: int, d_xcol: int,
+                           d_xval: int, d_bptr: int, d_bcol: int, d_bw: int,
+                           stream: int = 0) -> None:
+    _check(load().sptrsv_get_transformed(plan, d_new_level, d_xptr, d_xcol, d_xval,
+                                         d_bptr, d_bcol, d_bw, stream),
+           "sptrsv_get_transformed")
+
+
+def sptrsv_debug_inject_wait(plan: int, row: int) -> None:
+    _check(load().sptrsv_debug_inject_wait(plan, row), "sptrsv_debug_inject_wait")
+
+
+def sptrsv_set_profiling(plan: int, on: bool) -> None:
+    _check(load().sptrsv_set_profiling(plan, 1 if on else 0), "sptrsv_set_profiling")
+
+
+def sptrsv_last_kernel_ms(plan: int) -> float:
+    ms = ctypes.c_float()
+    _check(load().sptrsv_last_kernel_ms(plan, byref(ms)), "sptrsv_last_kernel_ms")
+    return float(ms.value)
+
+
+# --- torch convenience wrapper ---------------------------------------------
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Plan:
+    """Owns an sptrsv plan built from a CSR matrix held in torch tensors.
+
+    ``row_ptr``/``col`` int32 and ``val`` float64 CUDA tensors (or numpy
+    arrays, copied to the current device)."""
+
+    def __init__(self, n: int, row_ptr, col, val, stream=None):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+
+        def t(a, dt):
+            if isinstance(a, torch.Tensor):
+                return a.to(device=dev, dtype=dt).contiguous()
+            return torch.as_tensor(a, dtype=dt, device=dev).contiguous()
+
+        self.n = int(n)
+        rp, c, v = t(row_ptr, torch.int32), t(col, torch.int32), t(val, torch.float64)
+        self.nnz = int(c.numel())
+        self._handle = 0
+        self._handle = sptrsv_analyze(self.n, self.nnz, rp.data_ptr(), c.data_ptr(),
+                                      v.data_ptr(), _stream_handle(stream))
+
+    @property
+    def handle(self) -> int:
+        return self._handle
+
+    def transform(self, stream=None, **kw) -> "Plan":
+        prm = sptrsv_default_params()
+        for k, val in kw.items():
+            if not hasattr(prm, k):
+                raise TypeError(f"unknown transform parameter {k}")
+            setattr(prm, k, val)
+        sptrsv_transform(self._handle, prm, _stream_handle(stream))
+        return self
+
+    def solve(self, b, x=None, stream=None):
+        """x = L^{-1} b for b of shape (n,) or (n, nrhs), float64 on the GPU."""
+        import torch
+        if b.dtype != torch.float64 or not b.is_cuda or not b.is_contiguous():
+            raise TypeError("b must be a contiguous float64 CUDA tensor")
+        nrhs = 1 if b.dim() == 1 else int(b.shape[1])
+        if x is None:
+            x = torch.empty_like(b)
+        sptrsv_solve(self._handle, b.data_ptr(), x.data_ptr(), nrhs,
+                     _stream_handle(stream))
+        return x
+
+    def check(self, stream=None) -> None:
+        _check(sptrsv_check(self._handle, _stream_handle(stream)), "sptrsv_check")
+
+    def info(self) -> dict:
+        return sptrsv_get_info(self._handle).as_dict()
+
+    def levels(self):
+        import torch
+        inf = self.info()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        lv = torch.empty(self.n, dtype=torch.int32, device=dev)
+        lp = torch.empty(inf["nlev"] + 1, dtype=torch.int32, device=dev)
+        pm = torch.empty(self.n, dtype=torch.int32, device=dev)
+        sptrsv_get_levels(self._handle, lv.data_ptr(), lp.data_ptr(), pm.data_ptr(),
+                          _stream_handle(None))
+        return lv, lp, pm
+
+    def segments(self):
+        return sptrsv_get_segments(self._handle, self.info()["nlev_new"])
+
+    def transformed(self):
+        """The transformed rows in original order (see sptrsv_get_transformed)."""
+        import torch
+        inf = self.info()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        nl = torch.empty(self.n, dtype=torch.int32, device=dev)
+        xp = torch.empty(self.n + 1, dtype=torch.int64, device=dev)
+        bp = torch.empty(self.n + 1, dtype=torch.int64, device=dev)
+        xc = torch.empty(max(inf["nnz_x"], 1), dtype=torch.int32, device=dev)
+        xv = torch.empty(max(inf["nnz_x"], 1), dtype=torch.float64, device=dev)
+        bc = torch.empty(max(inf["nnz_b"], 1), dtype=torch.int32, device=dev)
+        bw = torch.empty(max(inf["nnz_b"], 1), dtype=torch.float64, device=dev)
+        sptrsv_get_transformed(self._handle, nl.data_ptr(), xp.data_ptr(), xc.data_ptr(),
+                               xv.data_ptr(), bp.data_ptr(), bc.data_ptr(), bw.data_ptr(),
+                               _stream_handle(None))
+        return dict(new_level=nl, xptr=xp, xcol=xc[:inf["nnz_x"]], xval=xv[:inf["nnz_x"]],
+                    bptr=bp, bcol=bc[:inf["nnz_b"]], bw=bw[:inf["nnz_b"]])
+
+    def close(self) -> None:
+        if self._handle:
+            sptrsv_plan_destroy(self._handle)
+            self._handle = 0
+
+    def __del__(self):  # pragma: no cover - interpreter shutdown order
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,975 @@
+// C entry points: plan life cycle, analysis and transform orchestration,
+// the thin-level selection heuristic, the solve dispatcher and the
+// launch-configuration autotuner.
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <functional>
+#include <map>
+#include <utility>
+
+#include "plan.cuh"
+
+using namespace sptrsv;
+
+namespace {
+
+sptrsv_status_t cuda_status(cudaError_t e) {
+    return e == cudaErrorMemoryAllocation ? SPTRSV_ERR_OOM : SPTRSV_ERR_CUDA;
+}
+
+#define CK(x)                                                                  \
+    do {                                                                       \
+        cudaError_t _e = (x);                                                  \
+        if (_e != cudaSuccess) {                                               \
+            (void)cudaGetLastError();                                          \
+            return cuda_status(_e);                                            \
+        }                                                                      \
+    } while (0)
+#define CKS(x)                                                                 \
+    do {                                                                       \
+        sptrsv_status_t _s = (x);                                              \
+        if (_s != SPTRSV_OK) return _s;                                        \
+    } while (0)
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+uint64_t timeout_ns(const sptrsv_plan_s *p) {
+    const int ms = p->prm.wait_timeout_ms > 0 ? p->prm.wait_timeout_ms : 5000;
+    return (uint64_t)ms * 1000000ull;
+}
+
+template <typename T>
+cudaError_t upload(DevArr<T> &d, const std::vector<T> &h, cudaStream_t s) {
+    cudaError_t e = d.alloc(h.size());
+    if (e != cudaSuccess || h.empty()) return e;
+    return cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+// Synchronise and surface a device-latched error.
+sptrsv_status_t sync_status(sptrsv_plan_t p, cudaStream_t s) {
+    CK(cudaStreamSynchronize(s));
+    DevStatus h;
+    CK(cudaMemcpy(&h, p->status.p, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h.code != 0) {
+        p->latched = (sptrsv_status_t)h.code;
+        return p->latched;
+    }
+    return SPTRSV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Thin-level selection heuristic H (the row choice the paper leaves to the
+// programmer, Sec. IV; its experiment removes thin levels at +10% FLOPs,
+// Sec. V).  Levels are scanned in order; a segment starts at a kept level t
+// and absorbs t+1, t+2, ... while the next level is thin (< tau rows), fewer
+// than d_max levels were absorbed, the rewrite fits the fill cap and the
+// FLOPs added over the whole matrix stay within rho * base_flops.
+// added(l, r, &cost) returns false when a row of level l would exceed the
+// fill cap when lifted to level l - r.
+std::vector<std::pair<int32_t, int32_t>> select_segments(
+    const std::vector<int64_t> &level_rows, int64_t tau, int32_t d_max, double rho,
+    int64_t base_flops, const std::function<bool(int32_t, int32_t, int64_t *)> &added) {
+    const int32_t nlev = (int32_t)level_rows.size();
+    const double budget = rho * (double)base_flops;
+    int64_t used = 0;
+    std::vector<std::pair<int32_t, int32_t>> segs;
+    int32_t lv = 0;
+    while (lv < nlev) {
+        const int32_t t = lv;
+        int32_t d = 0;
+        while (d < d_max && t + d + 1 < nlev && level_rows[t + d + 1] < tau) {
+            int64_t cost = 0;
+            if (!added(t + d + 1, d + 1, &cost)) break;
+            if ((double)(used + cost) > budget) break;
+            used += cost;
+            ++d;
+        }
+        segs.emplace_back(t, d);
+        lv = t + d + 1;
+    }
+    return segs;
+}
+
+// Evaluates candidate rewrites (level l lifted by r levels) on the device,
+// in batches, caching the results.
+struct FillOracle {
+    sptrsv_plan_t p;
+    cudaStream_t s;
+    int cap;
+    std::map<std::pair<int32_t, int32_t>, int64_t> cache;  // -1: overflow
+    sptrsv_status_t err = SPTRSV_OK;
+
+    sptrsv_status_t run(const std::vector<std::pair<int32_t, int32_t>> &qs_in) {
+        std::vector<int32_t> ql, qt;
+        std::vector<int64_t> qoff(1, 0);
+        for (auto &q : qs_in) {
+            if (cache.count(q)) continue;
+            const int32_t l = q.first, r = q.second;
+            ql.push_back(l);
+            qt.push_back(l - r);
+            qoff.push_back(qoff.back() + (p->h_level_ptr[l + 1] - p->h_level_ptr[l]));
+            cache[q] = -2;  // placeholder, filled below
+        }
+        const int32_t nq = (int32_t)ql.size();
+        if (nq == 0) return SPTRSV_OK;
+        const int64_t nitems = qoff.back();
+        DevArr<int32_t> d_ql, d_qt, irow, itgt, iq, ovf;
+        DevArr<int64_t> d_qoff;
+        DevArr<unsigned long long> added;
+        CK(upload(d_ql, ql, s));
+        CK(upload(d_qt, qt, s));
+        CK(upload(d_qoff, qoff, s));
+        CK(irow.alloc(nitems));
+        CK(itgt.alloc(nitems));
+        CK(iq.alloc(nitems));
+        CK(ovf.alloc(nq));
+        CK(added.alloc(nq));
+        CK(cudaMemsetAsync(ovf.p, 0, nq * sizeof(int32_t), s));
+        CK(cudaMemsetAsync(added.p, 0, nq * sizeof(unsigned long long), s));
+        CK(launch_expand_queries(nq, d_ql.p, d_qt.p, d_qoff.p, p->level_ptr.p, p->perm.p, irow.p,
+                                 itgt.p, iq.p, nullptr, s));
+        CK(launch_rewrite_count(nitems, irow.p, itgt.p, iq.p, p->row_ptr.p, p->col.p,
+                                p->level.p, cap, nullptr, added.p, ovf.p, p->num_sms, s));
+        std::vector<int32_t> h_ovf(nq);
+        std::vector<unsigned long long> h_add(nq);
+        CK(cudaMemcpyAsync(h_ovf.data(), ovf.p, nq * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h_add.data(), added.p, nq * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int32_t i = 0; i < nq; ++i)
+            cache[{ql[i], ql[i] - qt[i]}] = h_ovf[i] ? -1 : (int64_t)h_add[i];
+        return SPTRSV_OK;
+    }
+
+    // the rewrites H would query if nothing were cut, from segment start t
+    void optimistic_from(int32_t t, const std::vector<int64_t> &rows, int64_t tau, int32_t d_max,
+                         std::vector<std::pair<int32_t, int32_t>> &out) const {
+        const int32_t nlev = (int32_t)rows.size();
+        while (t < nlev) {
+            int32_t d = 0;
+            while (d < d_max && t + d + 1 < nlev && rows[t + d + 1] < tau) {
+                out.emplace_back(t + d + 1, d + 1);
+                ++d;
+            }
+            t += d + 1;
+        }
+    }
+};
+
+int64_t plain_flops(const sptrsv_plan_s *p) { return 2 * (p->nnz - p->n) + p->n; }
+
+sptrsv_status_t choose_segments(sptrsv_plan_t p, cudaStream_t s) {
+    const auto &prm = p->prm;
+    const int32_t nlev = p->nlev;
+    p->seg_first.clear();
+    p->seg_depth.clear();
+    if (prm.select_mode == SPTRSV_SELECT_NONE || nlev == 0) {
+        for (int32_t l = 0; l < nlev; ++l) {
+            p->seg_first.push_back(l);
+            p->seg_depth.push_back(0);
+        }
+        return SPTRSV_OK;
+    }
+    int64_t tau;
+    int32_t d_max;
+    double rho;
+    if (prm.select_mode == SPTRSV_SELECT_FIXED) {
+        tau = INT64_MAX;
+        d_max = prm.depth;
+        rho = INFINITY;
+    } else if (prm.select_mode == SPTRSV_SELECT_HEURISTIC) {
+        tau = prm.thin_rows;
+        d_max = prm.max_depth;
+        rho = prm.flop_budget;
+    } else {
+        return SPTRSV_ERR_UNSUPPORTED;
+    }
+    std::vector<int64_t> rows(nlev);
+    for (int32_t l = 0; l < nlev; ++l) rows[l] = p->h_level_ptr[l + 1] - p->h_level_ptr[l];
+    FillOracle fo{p, s, prm.max_row_fill};
+    // speculative batch: the uncut path plus every first step after a cut
+    std::vector<std::pair<int32_t, int32_t>> qs;
+    fo.optimistic_from(0, rows, tau, d_max, qs);
+    if (d_max > 0 && std::isfinite(rho))
+        for (int32_t l = 1; l < nlev; ++l)
+            if (rows[l] < tau) qs.emplace_back(l, 1);
+    CKS(fo.run(qs));
+    auto added = [&](int32_t l, int32_t r, int64_t *cost) -> bool {
+        auto it = fo.cache.find({l, r});
+        if (it == fo.cache.end()) {
+            std::vector<std::pair<int32_t, int32_t>> more;
+            fo.optimistic_from(l - r, rows, tau, d_max, more);
+            more.emplace_back(l, r);
+            fo.err = fo.run(more);
+            it = fo.cache.find({l, r});
+            if (fo.err != SPTRSV_OK || it == fo.cache.end()) return false;
+        }
+        if (it->second < 0) return false;
+        *cost = it->second;
+        return true;
+    };
+    auto segs = select_segments(rows, tau, d_max, rho, plain_flops(p), added);
+    if (fo.err != SPTRSV_OK) return fo.err;
+    for (auto &sg : segs) {
+        p->seg_first.push_back(sg.first);
+        p->seg_depth.push_back(sg.second);
+    }
+    return SPTRSV_OK;
+}
+
+// Rewritten rows of the chosen segments, computed on the device.
+sptrsv_status_t build_rewritten(sptrsv_plan_t p, cudaStream_t s) {
+    p->rw_off.reset();
+    p->rw_col.reset();
+    p->rw_val.reset();
+    p->rw_nb.reset();
+    p->pos_item.reset();
+    p->nitems = 0;
+    p->rows_rewritten = 0;
+    std::vector<int32_t> ql, qt;
+    std::vector<int64_t> qoff(1, 0);
+    for (size_t i = 0; i < p->seg_first.size(); ++i) {
+        const int32_t t = p->seg_first[i], d = p->seg_depth[i];
+        for (int32_t l = t + 1; l <= t + d; ++l) {
+            ql.push_back(l);
+            qt.push_back(t);
+            qoff.push_back(qoff.back() + (p->h_level_ptr[l + 1] - p->h_level_ptr[l]));
+        }
+    }
+    const int64_t nitems = qoff.back();
+    if (nitems == 0) return SPTRSV_OK;
+    const int32_t nq = (int32_t)ql.size();
+    DevArr<int32_t> d_ql, d_qt, irow, itgt, ipos, fill;
+    DevArr<int64_t> d_qoff, stmp;
+    CK(upload(d_ql, ql, s));
+    CK(upload(d_qt, qt, s));
+    CK(upload(d_qoff, qoff, s));
+    CK(irow.alloc(nitems));
+    CK(itgt.alloc(nitems));
+    CK(ipos.alloc(nitems));
+    CK(fill.alloc(nitems));
+    CK(launch_expand_queries(nq, d_ql.p, d_qt.p, d_qoff.p, p->level_ptr.p, p->perm.p, irow.p,
+                             itgt.p, nullptr, ipos.p, s));
+    const int cap = p->prm.max_row_fill;
+    CK(launch_rewrite_count(nitems, irow.p, itgt.p, nullptr, p->row_ptr.p, p->col.p, p->level.p,
+                            cap, fill.p, nullptr, nullptr, p->num_sms, s));
+    CK(p->rw_off.alloc(nitems + 1));
+    CK(stmp.alloc(scan_tmp_elems(nitems)));
+    CK(exclusive_scan_i32_i64(fill.p, p->rw_off.p, nitems, stmp.p, s));
+    int64_t total = 0;
+    CK(cudaMemcpyAsync(&total, p->rw_off.p + nitems, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (total < 0 || total > INT32_MAX) return SPTRSV_ERR_UNSUPPORTED;
+    CK(p->rw_col.alloc(total));
+    CK(p->rw_val.alloc(total));
+    CK(p->rw_nb.alloc(nitems));
+    CK(launch_rewrite_numeric(nitems, irow.p, itgt.p, p->rw_off.p, p->row_ptr.p, p->col.p,
+                              p->val.p, p->level.p, cap, p->rw_col.p, p->rw_val.p, p->rw_nb.p,
+                              p->status.p, p->num_sms, s));
+    CK(p->pos_item.alloc(p->n));
+    CK(launch_pos_item(p->n, nitems, ipos.p, p->pos_item.p, s));
+    CKS(sync_status(p, s));
+    p->nitems = nitems;
+    p->rows_rewritten = (int32_t)nitems;
+    return SPTRSV_OK;
+}
+
+// Level-ordered solve structure for layout L.
+template <typename T>
+sptrsv_status_t build_struct(sptrsv_plan_t p, SolveStruct<T> &ss, int L, cudaStream_t s) {
+    const int H = 32 / L;
+    const int32_t nseg = (int32_t)p->seg_first.size();
+    std::vector<int32_t> c_row0, c_nrows, lvl_chunk(nseg + 1, 0);
+    for (int32_t sg = 0; sg < nseg; ++sg) {
+        const int32_t t = p->seg_first[sg], d = p->seg_depth[sg];
+        const int32_t a = p->h_level_ptr[t], b = p->h_level_ptr[t + d + 1];
+        for (int32_t r = a; r < b; r += H) {
+            c_row0.push_back(r);
+            c_nrows.push_back(std::min<int32_t>(H, b - r));
+        }
+        lvl_chunk[sg + 1] = (int32_t)c_row0.size();
+    }
+    const int32_t nchunks = (int32_t)c_row0.size();
+    DevArr<int32_t> d_row0, d_nrows, d_width;
+    DevArr<int64_t> d_slots, d_off, stmp;
+    CK(upload(d_row0, c_row0, s));
+    CK(upload(d_nrows, c_nrows, s));
+    CK(upload(ss.lvl_chunk, lvl_chunk, s));
+    CK(d_width.alloc(nchunks));
+    CK(d_slots.alloc(nchunks));
+    CK(d_off.alloc((size_t)nchunks + 1));
+    CK(stmp.alloc(scan_tmp_elems(nchunks)));
+    const int32_t *pos_item = p->nitems > 0 ? p->pos_item.p : nullptr;
+    CK(launch_chunk_width(nchunks, d_row0.p, d_nrows.p, L, p->perm.p, p->offdeg.p, pos_item,
+                          p->rw_off.p, d_slots.p, d_width.p, s));
+    CK(exclusive_scan_i64_i64(d_slots.p, d_off.p, nchunks, stmp.p, s));
+    int64_t total = 0;
+    CK(cudaMemcpyAsync(&total, d_off.p + nchunks, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (total > INT32_MAX) return SPTRSV_ERR_UNSUPPORTED;
+    CK(ss.meta.alloc(nchunks));
+    CK(ss.ecol.alloc(total));
+    CK(ss.eval.alloc(total));
+    CK(ss.row_id.alloc(p->n));
+    CK(ss.diag.alloc(p->n));
+    CK(launch_chunk_fill<T>(nchunks, L, d_row0.p, d_nrows.p, d_width.p, d_off.p, p->perm.p,
+                            p->row_ptr.p, p->col.p, p->val.p, pos_item, p->rw_off.p,
+                            p->rw_col.p, p->rw_val.p, ss.meta.p, ss.ecol.p, ss.eval.p,
+                            ss.row_id.p, ss.diag.p, s));
+    CK(ss.chunk_level.alloc(nchunks));
+    CK(launch_chunk_level(nseg, ss.lvl_chunk.p, ss.chunk_level.p, s));
+    CK(cudaStreamSynchronize(s));
+    ss.nlev = nseg;
+    ss.nchunks = nchunks;
+    ss.L = L;
+    ss.nslots = total;
+    ss.built = true;
+    return SPTRSV_OK;
+}
+
+// Phases of the barrier kernel: maximal runs (>= 2) of consecutive levels of
+// at most run_rows rows become one CTA-local phase.
+template <typename T>
+sptrsv_status_t build_phases(sptrsv_plan_t p, SolveStruct<T> &ss, int run_rows, cudaStream_t s) {
+    std::vector<int2> ph;
+    const int32_t nseg = (int32_t)p->seg_first.size();
+    auto seg_rows = [&](int32_t sg) {
+        const int32_t t = p->seg_first[sg], d = p->seg_depth[sg];
+        return p->h_level_ptr[t + d + 1] - p->h_level_ptr[t];
+    };
+    int32_t sg = 0;
+    while (sg < nseg) {
+        if (run_rows > 0 && seg_rows(sg) <= run_rows) {
+            // runs are capped so that the CTAs waiting at the next grid
+            // barrier never wait longer than a fraction of the wait bound
+            constexpr int32_t kMaxRunLevels = 16384;
+            int32_t e = sg;
+            while (e < nseg && e - sg < kMaxRunLevels && seg_rows(e) <= run_rows) ++e;
+            if (e - sg >= 2) {
+                ph.push_back(make_int2(sg, -e));
+                sg = e;
+                continue;
+            }
+        }
+        ph.push_back(make_int2(sg, sg + 1));
+        ++sg;
+    }
+    CK(upload(ss.phases, ph, s));
+    CK(cudaStreamSynchronize(s));
+    ss.nphases = (int32_t)ph.size();
+    return SPTRSV_OK;
+}
+
+int auto_lanes(sptrsv_plan_t p) {
+    int64_t len = 0;
+    // average off-diagonal terms per row of the structure about to be built
+    len = (p->nnz - p->n);
+    if (p->nitems > 0) len += (p->nnz_x + p->nnz_b) - (p->nnz - p->n);
+    const double avg = p->n ? (double)len / p->n : 0.0;
+    if (avg <= 16) return 1;
+    if (avg <= 32) return 2;
+    if (avg <= 64) return 4;
+    return 8;
+}
+
+int grid_for(sptrsv_plan_t p, int nr, bool f32) {
+    const SolveConfig &c = p->cfg;
+    const int mx = f32 ? max_coresident_ctas<float>(c.L, nr, c.syncfree, c.block_threads, p->num_sms)
+                       : max_coresident_ctas<double>(c.L, nr, c.syncfree, c.block_threads, p->num_sms);
+    if (mx <= 0) return 0;
+    int g = c.grid > 0 ? c.grid : mx;
+    return std::min(g, mx);
+}
+
+// Count x and b terms of the solve structure (the info fields nnz_x/nnz_b).
+sptrsv_status_t count_terms(sptrsv_plan_t p, cudaStream_t s) {
+    const int32_t n = p->n;
+    if (n == 0) {
+        p->nnz_x = p->nnz_b = 0;
+        return SPTRSV_OK;
+    }
+    DevArr<int64_t> xc, bc, xs, bs, tmp;
+    CK(xc.alloc(n));
+    CK(bc.alloc(n));
+    CK(xs.alloc(n + 1));
+    CK(bs.alloc(n + 1));
+    CK(tmp.alloc(scan_tmp_elems(n)));
+    CK(launch_export_count(p->s64.nchunks, p->s64.L, p->s64.meta.p, p->s64.ecol.p,
+                           p->s64.row_id.p, xc.p, bc.p, s));
+    CK(exclusive_scan_i64_i64(xc.p, xs.p, n, tmp.p, s));
+    CK(exclusive_scan_i64_i64(bc.p, bs.p, n, tmp.p, s));
+    CK(cudaMemcpyAsync(&p->nnz_x, xs.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&p->nnz_b, bs.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t apply_config(sptrsv_plan_t p, cudaStream_t s) {
+    const bool f32 = p->prm.precision == SPTRSV_F32_IR;
+    if (p->s64.L != p->cfg.L || !p->s64.built) CKS(build_struct<double>(p, p->s64, p->cfg.L, s));
+    CKS(build_phases<double>(p, p->s64, p->cfg.cta_run_rows, s));
+    if (f32) {
+        if (p->s32.L != p->cfg.L || !p->s32.built)
+            CKS(build_struct<float>(p, p->s32, p->cfg.L, s));
+        CKS(build_phases<float>(p, p->s32, p->cfg.cta_run_rows, s));
+    }
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t nrhs,
+                           cudaStream_t s);
+
+// Times candidate launch configurations on the plan (median of 5 solves)
+// and keeps the fastest.
+sptrsv_status_t autotune(sptrsv_plan_t p, cudaStream_t s) {
+    const int32_t n = p->n;
+    if (n == 0) return SPTRSV_OK;
+    DevArr<double> b, x;
+    CK(b.alloc(n));
+    CK(x.alloc(n));
+    std::vector<double> ones(n, 1.0);
+    CK(cudaMemcpyAsync(b.p, ones.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto time_cfg = [&](double *ms_out) -> sptrsv_status_t {
+        CKS(apply_config(p, s));
+        for (int w = 0; w < 2; ++w) CKS(solve_impl(p, b.p, x.p, 1, s));
+        std::vector<float> t;
+        for (int r = 0; r < 5; ++r) {
+            CK(cudaEventRecord(e0, s));
+            CKS(solve_impl(p, b.p, x.p, 1, s));
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            t.push_back(ms);
+        }
+        CKS(sync_status(p, s));
+        std::sort(t.begin(), t.end());
+        *ms_out = t[t.size() / 2];
+        return SPTRSV_OK;
+    };
+    SolveConfig best = p->cfg;
+    double best_ms = 1e30;
+    std::vector<int> lanes = {1, 2, 4};
+    const int la = auto_lanes(p);
+    if (la > 4) lanes.push_back(la);
+    const int bt_req = p->prm.block_threads;
+    for (int L : lanes) {
+        if (p->prm.lanes_per_row > 0 && L != p->prm.lanes_per_row) continue;
+        for (int mode = 0; mode < 3; ++mode) {
+            SolveConfig c;
+            c.L = L;
+            c.syncfree = mode == 2;
+            c.block_threads = bt_req > 0 ? bt_req : 512;
+            c.grid = c.syncfree ? 0 : p->num_sms;
+            c.cta_run_rows = mode == 1 ? c.block_threads / L : 0;
+            if (p->prm.cta_run_rows < 0 && mode == 1) continue;
+            p->cfg = c;
+            double ms;
+            CKS(time_cfg(&ms));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+    }
+    // launch shape around the best layout and mode
+    const SolveConfig base = best;
+    for (int bt : {256, 512, 1024}) {
+        if (bt_req > 0 && bt != bt_req) continue;
+        for (int per_sm : {1, 2, 4}) {
+            SolveConfig c = base;
+            c.block_threads = bt;
+            c.grid = per_sm * p->num_sms;
+            if (c.cta_run_rows > 0) c.cta_run_rows = bt / c.L;
+            p->cfg = c;
+            if (grid_for(p, 1, p->prm.precision == SPTRSV_F32_IR) < c.grid) continue;
+            double ms;
+            CKS(time_cfg(&ms));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->cfg = best;
+    return apply_config(p, s);
+}
+
+void resolve_params(sptrsv_plan_t p, const sptrsv_transform_params_t *in) {
+    sptrsv_transform_params_t q = *in;
+    if (q.thin_rows <= 0) q.thin_rows = std::max(1, p->num_sms * 64 / 4);
+    if (q.max_depth <= 0) q.max_depth = q.max_depth == 0 ? 0 : 8;
+    if (q.max_depth > 16) q.max_depth = 16;
+    if (q.depth < 0) q.depth = 0;
+    if (q.depth > 16) q.depth = 16;
+    if (q.flop_budget < 0) q.flop_budget = 0.10;
+    if (q.max_row_fill <= 0) q.max_row_fill = 1024;
+    if (q.max_row_fill > 4096) q.max_row_fill = 4096;
+    if (q.ir_tol <= 0) q.ir_tol = 1e-15;
+    if (q.ir_max_iter < 0) q.ir_max_iter = 8;
+    if (q.ir_max_iter > 64) q.ir_max_iter = 64;
+    if (q.wait_timeout_ms <= 0) q.wait_timeout_ms = 5000;
+    p->prm = q;
+    p->thin_rows_used = q.thin_rows;
+}
+
+sptrsv_status_t ensure_ir(sptrsv_plan_t p, int64_t count) {
+    if ((int64_t)p->d32.n < count) CK(p->d32.alloc(count));
+    if ((int64_t)p->r64.n < count) CK(p->r64.alloc(count));
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t nrhs,
+                           cudaStream_t s) {
+    const int32_t n = p->n;
+    const uint64_t tmo = timeout_ns(p);
+    if (p->prm.precision != SPTRSV_F32_IR) {
+        const SolveData<double> sd = p->s64.view();
+        if (p->cfg.syncfree) {
+            // sentinel pre-fill first, so the events bracket the solve kernel alone
+            for (int32_t c0 = 0; c0 < nrhs; c0 += 32)
+                CK(launch_fill_sentinel<double>(x + c0, n, nrhs, std::min<int32_t>(32, nrhs - c0),
+                                                p->status.p, false, s));
+        }
+        if (p->profiling) CK(cudaEventRecord(p->prof_ev[0], s));
+        for (int32_t c0 = 0; c0 < nrhs; c0 += 32) {
+            const int nr = std::min<int32_t>(32, nrhs - c0);
+            LaunchCfg lc{p->cfg.block_threads, grid_for(p, nr, false)};
+            if (lc.grid <= 0) return SPTRSV_ERR_CUDA;
+            CK(launch_solve<double>(sd, b + c0, x + c0, n, nrhs, nr, p->cfg.syncfree, lc,
+                                    p->status.p, tmo, false, s, /*prefilled=*/true));
+        }
+        if (p->profiling) {
+            CK(cudaEventRecord(p->prof_ev[1], s));
+            p->prof_valid = true;
+        }
+        return SPTRSV_OK;
+    }
+    p->prof_valid = false;
+    // FP32 solve with FP64 iterative refinement
+    const int64_t count = (int64_t)n * nrhs;
+    CKS(ensure_ir(p, count));
+    const SolveData<float> sd = p->s32.view();
+    auto solve32 = [&](const double *rhs, bool skip) -> sptrsv_status_t {
+        for (int32_t c0 = 0; c0 < nrhs; c0 += 32) {
+            const int nr = std::min<int32_t>(32, nrhs - c0);
+            LaunchCfg lc{p->cfg.block_threads, grid_for(p, nr, true)};
+            if (lc.grid <= 0) return SPTRSV_ERR_CUDA;
+            CK(launch_solve<float>(sd, rhs + c0, p->d32.p + c0, n, nrhs, nr, p->cfg.syncfree,
+                                   lc, p->status.p, tmo, skip, s));
+        }
+        return SPTRSV_OK;
+    };
+    CK(launch_ir_begin(p->status.p, b, count, s));
+    CKS(solve32(b, false));
+    CK(launch_ir_update(x, p->d32.p, count, true, p->status.p, s));
+    for (int it = 0; it < p->prm.ir_max_iter; ++it) {
+        CK(launch_residual(n, p->row_ptr.p, p->col.p, p->val.p, b, x, p->r64.p, nrhs, nrhs,
+                           p->status.p, s));
+        CK(launch_ir_decide(p->status.p, p->prm.ir_tol, p->lnorm.p, s));
+        CKS(solve32(p->r64.p, true));
+        CK(launch_ir_update(x, p->d32.p, count, false, p->status.p, s));
+    }
+    return SPTRSV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sptrsv_status_string(sptrsv_status_t s) {
+    switch (s) {
+    case SPTRSV_OK: return "ok";
+    case SPTRSV_ERR_INVALID_ARG: return "invalid argument";
+    case SPTRSV_ERR_NOT_LOWER: return "matrix is not lower triangular (or column out of range)";
+    case SPTRSV_ERR_UNSORTED: return "CSR row pointers or columns are not sorted";
+    case SPTRSV_ERR_ZERO_DIAG: return "zero on the diagonal";
+    case SPTRSV_ERR_MISSING_DIAG: return "diagonal entry missing";
+    case SPTRSV_ERR_OOM: return "device out of memory";
+    case SPTRSV_ERR_CUDA: return "CUDA runtime error";
+    case SPTRSV_ERR_TIMEOUT: return "a bounded device wait timed out";
+    case SPTRSV_ERR_BAD_STATE: return "plan in a bad state (call order or earlier failure)";
+    case SPTRSV_ERR_UNSUPPORTED: return "unsupported size or mode";
+    }
+    return "unknown status";
+}
+
+void sptrsv_default_params(sptrsv_transform_params_t *prm) {
+    if (!prm) return;
+    std::memset(prm, 0, sizeof(*prm));
+    prm->select_mode = SPTRSV_SELECT_HEURISTIC;
+    prm->depth = 2;
+    prm->thin_rows = 0;
+    prm->max_depth = 8;
+    prm->flop_budget = 0.10;
+    prm->max_row_fill = 1024;
+    prm->solve_mode = SPTRSV_SOLVE_AUTO;
+    prm->precision = SPTRSV_F64;
+    prm->ir_tol = 1e-15;
+    prm->ir_max_iter = 8;
+    prm->lanes_per_row = 0;
+    prm->block_threads = 0;
+    prm->cta_run_rows = 0;
+    prm->wait_timeout_ms = 5000;
+}
+
+sptrsv_status_t sptrsv_analyze(int32_t n, int64_t nnz, const int32_t *d_row_ptr,
+                               const int32_t *d_col, const double *d_val,
+                               sptrsv_stream_t stream, sptrsv_plan_t *out) {
+    if (!out) return SPTRSV_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 0 || nnz < 0 || nnz > INT32_MAX) return SPTRSV_ERR_INVALID_ARG;
+    if (n > 0 && (!d_row_ptr || (nnz > 0 && (!d_col || !d_val)))) return SPTRSV_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double t0 = now_ms();
+    sptrsv_plan_s *p = new sptrsv_plan_s();
+    auto fail = [&](sptrsv_status_t st) {
+        delete p;
+        return st;
+    };
+    auto cuda_fail = [&](cudaError_t e) {
+        (void)cudaGetLastError();
+        delete p;
+        return cuda_status(e);
+    };
+#define CKP(x)                                                                 \
+    do {                                                                       \
+        cudaError_t _e = (x);                                                  \
+        if (_e != cudaSuccess) return cuda_fail(_e);                           \
+    } while (0)
+    CKP(cudaGetDevice(&p->device));
+    CKP(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+    p->n = n;
+    p->nnz = nnz;
+    sptrsv_default_params(&p->prm);
+    p->prm.select_mode = SPTRSV_SELECT_NONE;
+    p->prm.solve_mode = SPTRSV_SOLVE_BARRIER;
+    resolve_params(p, &p->prm);
+    CKP(p->status.alloc(1));
+    CKP(cudaMemsetAsync(p->status.p, 0, sizeof(DevStatus), s));
+    CKP(p->lnorm.alloc(1));
+    CKP(cudaMemsetAsync(p->lnorm.p, 0, sizeof(unsigned long long), s));
+    CKP(p->row_ptr.alloc((size_t)n + 1));
+    CKP(p->col.alloc(nnz));
+    CKP(p->val.alloc(nnz));
+    if (n == 0) {
+        p->nlev = 0;
+        p->h_level_ptr.assign(1, 0);
+        CKP(p->level_ptr.alloc(1));
+        CKP(cudaMemsetAsync(p->level_ptr.p, 0, sizeof(int32_t), s));
+        CKP(cudaStreamSynchronize(s));
+        p->analyze_ms = now_ms() - t0;
+        *out = p;
+        return SPTRSV_OK;
+    }
+    CKP(cudaMemcpyAsync(p->row_ptr.p, d_row_ptr, ((size_t)n + 1) * sizeof(int32_t),
+                        cudaMemcpyDeviceToDevice, s));
+    if (nnz > 0) {
+        CKP(cudaMemcpyAsync(p->col.p, d_col, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        CKP(cudaMemcpyAsync(p->val.p, d_val, nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    // validation
+    DevArr<unsigned long long> err;
+    CKP(err.alloc(1));
+    CKP(cudaMemsetAsync(err.p, 0xff, sizeof(unsigned long long), s));
+    CKP(p->offdeg.alloc(n));
+    CKP(launch_validate(n, nnz, p->row_ptr.p, p->col.p, p->val.p, p->offdeg.p, err.p,
+                        p->lnorm.p, s));
+    unsigned long long h_err = 0;
+    CKP(cudaMemcpyAsync(&h_err, err.p, sizeof(h_err), cudaMemcpyDeviceToHost, s));
+    CKP(cudaStreamSynchronize(s));
+    if (h_err != ~0ull) return fail((sptrsv_status_t)(h_err & 0xff));
+    // successor lists (transpose of the strict lower part)
+    const int64_t nsucc = nnz - n;
+    DevArr<int32_t> tcnt, tptr, tcur, tidx;
+    DevArr<int64_t> stmp;
+    CKP(tcnt.alloc(n));
+    CKP(tptr.alloc((size_t)n + 1));
+    CKP(tcur.alloc(n));
+    CKP(tidx.alloc(nsucc > 0 ? nsucc : 1));
+    CKP(stmp.alloc(scan_tmp_elems(n)));
+    CKP(cudaMemsetAsync(tcnt.p, 0, n * sizeof(int32_t), s));
+    CKP(cudaMemsetAsync(tcur.p, 0, n * sizeof(int32_t), s));
+    CKP(launch_count_succ(n, p->row_ptr.p, p->col.p, tcnt.p, s));
+    CKP(exclusive_scan_i32_i32(tcnt.p, tptr.p, n, stmp.p, s));
+    CKP(launch_fill_succ(n, p->row_ptr.p, p->col.p, tptr.p, tcur.p, tidx.p, s));
+    // levels by breadth-first traversal
+    DevArr<int32_t> indeg, queue, cnt3, lstart, nlev_d;
+    CKP(indeg.alloc(n));
+    CKP(queue.alloc(n));
+    CKP(cnt3.alloc(3));
+    CKP(lstart.alloc((size_t)n + 1));
+    CKP(nlev_d.alloc(1));
+    CKP(p->level.alloc(n));
+    CKP(cudaMemcpyAsync(indeg.p, p->offdeg.p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    CKP(cudaMemsetAsync(cnt3.p, 0, 3 * sizeof(int32_t), s));
+    CKP(launch_bfs_levels(n, tptr.p, tidx.p, indeg.p, p->level.p, queue.p, cnt3.p, lstart.p,
+                          nlev_d.p, p->status.p, timeout_ns(p), p->num_sms, s));
+    int32_t nlev = 0;
+    CKP(cudaMemcpyAsync(&nlev, nlev_d.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    {
+        sptrsv_status_t st = sync_status(p, s);
+        if (st != SPTRSV_OK) return fail(st);
+    }
+    if (nlev <= 0) return fail(SPTRSV_ERR_BAD_STATE);
+    p->nlev = nlev;
+    p->h_level_ptr.resize((size_t)nlev + 1);
+    CKP(cudaMemcpy(p->h_level_ptr.data(), lstart.p, ((size_t)nlev + 1) * sizeof(int32_t),
+                   cudaMemcpyDeviceToHost));
+    if (p->h_level_ptr[nlev] != n) return fail(SPTRSV_ERR_BAD_STATE);
+    CKP(p->level_ptr.alloc((size_t)nlev + 1));
+    CKP(cudaMemcpyAsync(p->level_ptr.p, lstart.p, ((size_t)nlev + 1) * sizeof(int32_t),
+                        cudaMemcpyDeviceToDevice, s));
+    // rows ordered by (level, row)
+    CKP(p->perm.alloc(n));
+    {
+        DevArr<char> rtmp;
+        CKP(rtmp.alloc(radix_tmp_bytes(n)));
+        CKP(launch_level_perm(n, p->level.p, nlev, p->perm.p, rtmp.p, s));
+        CKP(cudaStreamSynchronize(s));
+    }
+    // plain level-set structure
+    {
+        sptrsv_status_t st = choose_segments(p, s);
+        if (st == SPTRSV_OK) {
+            p->cfg = SolveConfig{};
+            p->cfg.L = 1;
+            p->cfg.block_threads = 512;
+            p->cfg.grid = p->num_sms;
+            p->cfg.cta_run_rows = 0;
+            st = apply_config(p, s);
+        }
+        if (st == SPTRSV_OK) st = count_terms(p, s);
+        if (st != SPTRSV_OK) return fail(st);
+    }
+#undef CKP
+    p->analyze_ms = now_ms() - t0;
+    *out = p;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_transform(sptrsv_plan_t p, const sptrsv_transform_params_t *prm,
+                                 sptrsv_stream_t stream) {
+    if (!p || !prm) return SPTRSV_ERR_INVALID_ARG;
+    if (p->latched != SPTRSV_OK) return SPTRSV_ERR_BAD_STATE;
+    if (prm->select_mode < 0 || prm->select_mode > 3 || prm->solve_mode < 0 ||
+        prm->solve_mode > 2 || (prm->precision != SPTRSV_F64 && prm->precision != SPTRSV_F32_IR))
+        return SPTRSV_ERR_INVALID_ARG;
+    if (prm->lanes_per_row != 0 && prm->lanes_per_row != 1 && prm->lanes_per_row != 2 &&
+        prm->lanes_per_row != 4 && prm->lanes_per_row != 8 && prm->lanes_per_row != 16 &&
+        prm->lanes_per_row != 32)
+        return SPTRSV_ERR_INVALID_ARG;
+    if (prm->block_threads != 0 &&
+        (prm->block_threads < 64 || prm->block_threads > 1024 || prm->block_threads % 32))
+        return SPTRSV_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double t0 = now_ms();
+    resolve_params(p, prm);
+    if (p->n == 0) {
+        p->transform_ms = now_ms() - t0;
+        return SPTRSV_OK;
+    }
+    p->s64 = SolveStruct<double>{};
+    p->s32 = SolveStruct<float>{};
+    CKS(choose_segments(p, s));
+    CKS(build_rewritten(p, s));
+    // provisional config: requested or default launch shape
+    SolveConfig c;
+    c.syncfree = p->prm.solve_mode == SPTRSV_SOLVE_SYNCFREE;
+    c.block_threads = p->prm.block_threads > 0 ? p->prm.block_threads : 512;
+    c.grid = c.syncfree ? 0 : p->num_sms;
+    c.L = 1;
+    p->cfg = c;
+    CKS(build_struct<double>(p, p->s64, 1, s));
+    CKS(count_terms(p, s));
+    c.L = p->prm.lanes_per_row > 0 ? p->prm.lanes_per_row : auto_lanes(p);
+    c.cta_run_rows = p->prm.cta_run_rows < 0 ? 0
+                     : p->prm.cta_run_rows > 0 ? p->prm.cta_run_rows
+                                               : c.block_threads / c.L;
+    if (c.syncfree) c.cta_run_rows = 0;
+    p->cfg = c;
+    CKS(apply_config(p, s));
+    if (p->prm.solve_mode == SPTRSV_SOLVE_AUTO) CKS(autotune(p, s));
+    CKS(sync_status(p, s));
+    p->transform_ms = now_ms() - t0;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_solve(sptrsv_plan_t p, const double *d_b, double *d_x, int32_t nrhs,
+                             sptrsv_stream_t stream) {
+    if (!p) return SPTRSV_ERR_INVALID_ARG;
+    if (p->latched != SPTRSV_OK) return SPTRSV_ERR_BAD_STATE;
+    if (nrhs < 1) return SPTRSV_ERR_INVALID_ARG;
+    if (p->n == 0) return SPTRSV_OK;
+    if (!d_b || !d_x) return SPTRSV_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)p->n * nrhs * sizeof(double);
+    const char *b0 = (const char *)d_b, *x0 = (const char *)d_x;
+    if (b0 < x0 + bytes && x0 < b0 + bytes) return SPTRSV_ERR_INVALID_ARG;
+    return solve_impl(p, d_b, d_x, nrhs, (cudaStream_t)stream);
+}
+
+sptrsv_status_t sptrsv_check(sptrsv_plan_t p, sptrsv_stream_t stream) {
+    if (!p) return SPTRSV_ERR_INVALID_ARG;
+    if (p->latched != SPTRSV_OK) return p->latched;
+    return sync_status(p, (cudaStream_t)stream);
+}
+
+sptrsv_status_t sptrsv_get_info(sptrsv_plan_t p, sptrsv_info_t *o) {
+    if (!p || !o) return SPTRSV_ERR_INVALID_ARG;
+    std::memset(o, 0, sizeof(*o));
+    o->n = p->n;
+    o->nnz = p->nnz;
+    o->nlev = p->nlev;
+    o->nlev_new = (int32_t)p->seg_first.size();
+    o->rows_rewritten = p->rows_rewritten;
+    o->nnz_x = p->nnz_x;
+    o->nnz_b = p->nnz_b;
+    o->flops_plain = plain_flops(p);
+    o->flops_new = 2 * (p->nnz_x + p->nnz_b) + p->n;
+    o->select_mode = p->prm.select_mode;
+    o->solve_mode = p->cfg.syncfree ? SPTRSV_SOLVE_SYNCFREE : SPTRSV_SOLVE_BARRIER;
+    o->precision = p->prm.precision;
+    o->lanes_per_row = p->cfg.L;
+    o->block_threads = p->cfg.block_threads;
+    o->grid_blocks = p->n ? grid_for(p, 1, p->prm.precision == SPTRSV_F32_IR) : 0;
+    o->cta_run_rows = p->cfg.cta_run_rows;
+    o->thin_rows = p->thin_rows_used;
+    o->max_depth = p->prm.max_depth;
+    o->flop_budget = p->prm.flop_budget;
+    o->num_sms = p->num_sms;
+    o->analyze_ms = p->analyze_ms;
+    o->transform_ms = p->transform_ms;
+    if (p->status.p) {
+        DevStatus h;
+        if (cudaMemcpy(&h, p->status.p, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess)
+            o->ir_iters_last = h.ir_iters;
+    }
+    return SPTRSV_OK;
+}
+
+void sptrsv_plan_destroy(sptrsv_plan_t p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    delete p;
+}
+
+sptrsv_status_t sptrsv_get_levels(sptrsv_plan_t p, int32_t *d_level, int32_t *d_level_ptr,
+                                  int32_t *d_perm, sptrsv_stream_t stream) {
+    if (!p) return SPTRSV_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->n == 0) {
+        if (d_level_ptr) CK(cudaMemsetAsync(d_level_ptr, 0, sizeof(int32_t), s));
+        CK(cudaStreamSynchronize(s));
+        return SPTRSV_OK;
+    }
+    if (d_level)
+        CK(cudaMemcpyAsync(d_level, p->level.p, p->n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    if (d_level_ptr)
+        CK(cudaMemcpyAsync(d_level_ptr, p->level_ptr.p, ((size_t)p->nlev + 1) * sizeof(int32_t),
+                           cudaMemcpyDeviceToDevice, s));
+    if (d_perm)
+        CK(cudaMemcpyAsync(d_perm, p->perm.p, p->n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_get_segments(sptrsv_plan_t p, int32_t *h_first, int32_t *h_depth) {
+    if (!p) return SPTRSV_ERR_INVALID_ARG;
+    for (size_t i = 0; i < p->seg_first.size(); ++i) {
+        if (h_first) h_first[i] = p->seg_first[i];
+        if (h_depth) h_depth[i] = p->seg_depth[i];
+    }
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_get_transformed(sptrsv_plan_t p, int32_t *d_new_level, int64_t *d_xptr,
+                                       int32_t *d_xcol, double *d_xval, int64_t *d_bptr,
+                                       int32_t *d_bcol, double *d_bw, sptrsv_stream_t stream) {
+    if (!p) return SPTRSV_ERR_INVALID_ARG;
+    if (p->latched != SPTRSV_OK) return SPTRSV_ERR_BAD_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int32_t n = p->n;
+    if (n == 0) return SPTRSV_OK;
+    if ((d_xcol || d_xval) && !d_xptr) return SPTRSV_ERR_INVALID_ARG;
+    if ((d_bcol || d_bw) && !d_bptr) return SPTRSV_ERR_INVALID_ARG;
+    DevArr<int64_t> xc, bc, tmp, xp, bp;
+    CK(xc.alloc(n));
+    CK(bc.alloc(n));
+    CK(tmp.alloc(scan_tmp_elems(n)));
+    CK(launch_export_count(p->s64.nchunks, p->s64.L, p->s64.meta.p, p->s64.ecol.p,
+                           p->s64.row_id.p, xc.p, bc.p, s));
+    int64_t *xptr = d_xptr, *bptr = d_bptr;
+    if (!xptr) {
+        CK(xp.alloc(n + 1));
+        xptr = xp.p;
+    }
+    if (!bptr) {
+        CK(bp.alloc(n + 1));
+        bptr = bp.p;
+    }
+    CK(exclusive_scan_i64_i64(xc.p, xptr, n, tmp.p, s));
+    CK(exclusive_scan_i64_i64(bc.p, bptr, n, tmp.p, s));
+    CK(launch_export_fill(p->s64.nchunks, p->s64.L, p->s64.meta.p, p->s64.ecol.p, p->s64.eval.p,
+                          p->s64.row_id.p, p->s64.chunk_level.p, xptr, bptr, d_xcol, d_xval,
+                          d_bcol, d_bw, d_new_level, s));
+    CK(cudaStreamSynchronize(s));
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_set_profiling(sptrsv_plan_t p, int32_t on) {
+    if (!p) return SPTRSV_ERR_INVALID_ARG;
+    if (on && !p->prof_ev[0]) {
+        CK(cudaEventCreate(&p->prof_ev[0]));
+        CK(cudaEventCreate(&p->prof_ev[1]));
+    }
+    p->profiling = on != 0;
+    p->prof_valid = false;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_last_kernel_ms(sptrsv_plan_t p, float *ms) {
+    if (!p || !ms) return SPTRSV_ERR_INVALID_ARG;
+    if (!p->prof_valid) return SPTRSV_ERR_BAD_STATE;
+    CK(cudaEventSynchronize(p->prof_ev[1]));
+    CK(cudaEventElapsedTime(ms, p->prof_ev[0], p->prof_ev[1]));
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_debug_inject_wait(sptrsv_plan_t p, int32_t row) {
+    if (!p || row < 0 || row >= p->n) return SPTRSV_ERR_INVALID_ARG;
+    if (p->latched != SPTRSV_OK) return SPTRSV_ERR_BAD_STATE;
+    // find the row's solve position and chunk on the host, then rewrite its
+    // first slot (a padded slot is added if the row has none) to read x[row]
+    std::vector<int32_t> row_id(p->n);
+    CK(cudaMemcpy(row_id.data(), p->s64.row_id.p, p->n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    int32_t pos = -1;
+    for (int32_t i = 0; i < p->n; ++i)
+        if (row_id[i] == row) { pos = i; break; }
+    if (pos < 0) return SPTRSV_ERR_BAD_STATE;
+    std::vector<int4> meta(p->s64.nchunks);
+    CK(cudaMemcpy(meta.data(), p->s64.meta.p, meta.size() * sizeof(int4), cudaMemcpyDeviceToHost));
+    for (int32_t c = 0; c < p->s64.nchunks; ++c) {
+        const int4 m = meta[c];
+        if (pos < m.x || pos >= m.x + m.y) continue;
+        if (m.z == 0) return SPTRSV_ERR_UNSUPPORTED;  // row without any slot
+        const int32_t k = pos - m.x;
+        const int64_t slot = (int64_t)m.w + (int64_t)k * p->s64.L;
+        CK(cudaMemcpy(p->s64.ecol.p + slot, &row, sizeof(int32_t), cudaMemcpyHostToDevice));
+        if (p->s32.built)
+            CK(cudaMemcpy(p->s32.ecol.p + slot, &row, sizeof(int32_t), cudaMemcpyHostToDevice));
+        return SPTRSV_OK;
+    }
+    return SPTRSV_ERR_BAD_STATE;
+}
+
+}  // extern "C"

@@ -1,0 +1,155 @@
+// Device helpers shared by the library's kernels: status latching, bounded
+// waits, gpu-scope relaxed/acquire memory operations, the grid barrier of the
+// persistent level-set solve and the "not yet computed" sentinels of the
+// synchronisation-free solve.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/sptrsv.h"
+
+namespace sptrsv {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+// Entry encoding of the solve structure: col >= 0 reads x[col], col < 0
+// (but not PAD) reads b[~col] (a right-hand-side term of a rewritten row),
+// PAD is a padding slot.
+constexpr int32_t PAD_COL = INT32_MIN;
+
+// Device status block of a plan (zeroed at creation):
+//  [0] error code (first one wins), [1] row or index involved,
+//  [2] abort flag (set on any error: every wait returns), [3] spare,
+//  [4..5] barrier arrival counter (u64), [6..7] exit counter (u64).
+struct DevStatus {
+    int32_t code;
+    int32_t where;
+    int32_t abort;
+    int32_t ir_iters;
+    unsigned long long bar_count;
+    unsigned long long exit_count;
+    unsigned long long ir_flag;   // refinement converged flag
+    double norms[4];              // scratch for infinity norms (as u64 bits)
+};
+
+__device__ __forceinline__ void latch_error(DevStatus *st, int code, int where) {
+    if (atomicCAS(&st->code, 0, code) == 0) st->where = where;
+    atomicExch(&st->abort, 1);
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_relaxed_i32(const int32_t *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const void *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed_u32(const void *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(void *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_u32(void *p, unsigned v) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+
+// "Not computed yet" markers of the synchronisation-free solve: signalling
+// NaNs with a payload.  Arithmetic never produces a signalling NaN, so a
+// computed unknown can never look like the marker.
+template <typename T> struct Sentinel;
+template <> struct Sentinel<double> {
+    using Bits = unsigned long long;
+    static constexpr Bits bits = 0x7FF4DEADBEEF0001ull;
+};
+template <> struct Sentinel<float> {
+    using Bits = unsigned;
+    static constexpr Bits bits = 0x7FA0BEEFu;
+};
+
+// Bounded wait bookkeeping: every spin in the library checks the plan's
+// abort flag and a deadline on the global timer every `kPollMask + 1`
+// iterations and gives up (latching SPTRSV_ERR_TIMEOUT) past the deadline.
+constexpr int kPollMask = 63;
+
+struct WaitBudget {
+    uint64_t deadline;
+    __device__ __forceinline__ explicit WaitBudget(uint64_t timeout_ns)
+        : deadline(0) { deadline = globaltimer_ns() + timeout_ns; }
+    // true if the wait must stop (timeout latched or someone else aborted)
+    __device__ __forceinline__ bool expired(DevStatus *st, int where) {
+        if (ld_relaxed_i32(&st->abort)) return true;
+        if (globaltimer_ns() > deadline) {
+            latch_error(st, SPTRSV_ERR_TIMEOUT, where);
+            return true;
+        }
+        return false;
+    }
+};
+
+// Grid-wide barrier for a co-resident (cooperatively launched) grid.  The
+// arrival counter only grows inside one launch; `target` is
+// (barrier index + 1) * gridDim.x.  Returns false if the wait gave up.
+__device__ __forceinline__ bool grid_barrier(DevStatus *st, unsigned long long target,
+                                             uint64_t timeout_ns, int where) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();  // publish this CTA's stores before arriving
+        red_release_add_u64(&st->bar_count, 1ull);
+        if (ld_acquire_u64(&st->bar_count) < target) {
+            WaitBudget wb(timeout_ns);
+            unsigned it = 0;
+            while (ld_acquire_u64(&st->bar_count) < target) {
+                if ((++it & kPollMask) == 0 && wb.expired(st, where)) { ok = 0; break; }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Called once by every CTA at the very end of a kernel that used
+// grid_barrier: the last CTA to leave resets the counters for the next
+// launch on the same stream.
+__device__ __forceinline__ void grid_exit(DevStatus *st) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned long long prev = atomicAdd(&st->exit_count, 1ull);
+        if (prev == gridDim.x - 1) {
+            atomicExch(&st->bar_count, 0ull);
+            atomicExch(&st->exit_count, 0ull);
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace sptrsv

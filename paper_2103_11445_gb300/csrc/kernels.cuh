@@ -1,0 +1,51 @@
+// Host-side launchers of the library's kernels (one group per .cu file).
+// All launchers are stream-ordered and return the cudaError_t of the launch.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace sptrsv {
+
+// ---- scan.cu --------------------------------------------------------------
+// out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
+// `tmp` must hold scan_tmp_elems(n) int64 values.
+int64_t scan_tmp_elems(int64_t n);
+cudaError_t exclusive_scan_i32_i64(const int32_t *in, int64_t *out, int64_t n,
+                                   int64_t *tmp, cudaStream_t s);
+cudaError_t exclusive_scan_i64_i64(const int64_t *in, int64_t *out, int64_t n,
+                                   int64_t *tmp, cudaStream_t s);
+cudaError_t exclusive_scan_i32_i32(const int32_t *in, int32_t *out, int64_t n,
+                                   int64_t *tmp, cudaStream_t s);
+
+// ---- analyze.cu -----------------------------------------------------------
+// Validation: err (u64, host-initialised to ~0) receives min(row<<8 | code)
+// over bad rows; offdeg[i] = off-diagonal count; lnorm (u64 bits) = max row
+// abs sum.
+cudaError_t launch_validate(int32_t n, int64_t nnz, const int32_t *row_ptr,
+                            const int32_t *col, const double *val,
+                            int32_t *offdeg, unsigned long long *err,
+                            unsigned long long *lnorm, cudaStream_t s);
+// Successor (transposed strict-lower) lists.
+cudaError_t launch_count_succ(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                              int32_t *tcnt, cudaStream_t s);
+cudaError_t launch_fill_succ(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                             const int32_t *tptr, int32_t *tcur, int32_t *tidx,
+                             cudaStream_t s);
+// Level analysis by breadth-first traversal (Kahn) in one cooperative
+// launch.  indeg is consumed.  level_start[0..nlev] receives the queue
+// offset of every level, *nlev_out the level count.  cnt3 = 3 zeroed ints.
+cudaError_t launch_bfs_levels(int32_t n, const int32_t *tptr, const int32_t *tidx,
+                              int32_t *indeg, int32_t *level, int32_t *queue,
+                              int32_t *cnt3, int32_t *level_start,
+                              int32_t *nlev_out, DevStatus *st,
+                              uint64_t timeout_ns, int num_sms, cudaStream_t s);
+// perm = rows ordered by (level, row), via a stable LSD radix sort.
+// tmp must hold radix_tmp_bytes(n) bytes.
+size_t radix_tmp_bytes(int32_t n);
+cudaError_t launch_level_perm(int32_t n, const int32_t *level, int32_t nlev,
+                              int32_t *perm, void *tmp, cudaStream_t s);
+
+}  // namespace sptrsv

@@ -1,0 +1,127 @@
+// Host-side plan object shared by the C entry points (api.cu) and the
+// batched solve (batch.cu).
+#pragma once
+
+#include <cstring>
+#include <vector>
+
+#include "solve.cuh"
+#include "transform.cuh"
+
+namespace sptrsv {
+
+// Owning device array (cudaMalloc / cudaFree).
+template <typename T>
+struct DevArr {
+    T *p = nullptr;
+    size_t n = 0;
+    DevArr() = default;
+    DevArr(const DevArr &) = delete;
+    DevArr &operator=(const DevArr &) = delete;
+    DevArr(DevArr &&o) noexcept { swap(o); }
+    DevArr &operator=(DevArr &&o) noexcept {
+        if (this != &o) {
+            reset();
+            swap(o);
+        }
+        return *this;
+    }
+    ~DevArr() { reset(); }
+    void reset() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    cudaError_t alloc(size_t count) {
+        reset();
+        if (count == 0) return cudaSuccess;
+        cudaError_t e = cudaMalloc((void **)&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        n = count;
+        return cudaSuccess;
+    }
+    void swap(DevArr &o) {
+        std::swap(p, o.p);
+        std::swap(n, o.n);
+    }
+};
+
+template <typename T>
+struct SolveStruct {
+    DevArr<int32_t> lvl_chunk, ecol, row_id, chunk_level;
+    DevArr<int4> meta;
+    DevArr<T> eval, diag;
+    DevArr<int2> phases;
+    int32_t nlev = 0, nchunks = 0, L = 1, nphases = 0;
+    int64_t nslots = 0;
+    bool built = false;
+    SolveData<T> view() const {
+        SolveData<T> v;
+        v.nlev = nlev;
+        v.nchunks = nchunks;
+        v.L = L;
+        v.lvl_chunk = lvl_chunk.p;
+        v.meta = meta.p;
+        v.ecol = ecol.p;
+        v.eval = eval.p;
+        v.row_id = row_id.p;
+        v.diag = diag.p;
+        v.phases = phases.p;
+        v.nphases = nphases;
+        return v;
+    }
+};
+
+struct SolveConfig {
+    bool syncfree = false;
+    int L = 1;
+    int block_threads = 512;
+    int grid = 0;
+    int cta_run_rows = 0;   // resolved threshold (<= 0: no runs)
+};
+
+}  // namespace sptrsv
+
+struct sptrsv_plan_s {
+    int device = 0;
+    int num_sms = 0;
+    int32_t n = 0;
+    int64_t nnz = 0;
+    sptrsv::DevArr<int32_t> row_ptr, col;
+    sptrsv::DevArr<double> val;
+    sptrsv::DevArr<int32_t> offdeg, level, level_ptr, perm;
+    std::vector<int32_t> h_level_ptr;
+    int32_t nlev = 0;
+    sptrsv::DevArr<sptrsv::DevStatus> status;
+    sptrsv::DevArr<unsigned long long> lnorm;
+    // transform
+    std::vector<int32_t> seg_first, seg_depth;
+    sptrsv::DevArr<int64_t> rw_off;
+    sptrsv::DevArr<int32_t> rw_col, rw_nb, pos_item;
+    sptrsv::DevArr<double> rw_val;
+    int64_t nitems = 0;
+    int64_t nnz_x = 0, nnz_b = 0;
+    int32_t rows_rewritten = 0;
+    sptrsv::SolveStruct<double> s64;
+    sptrsv::SolveStruct<float> s32;
+    sptrsv_transform_params_t prm{};
+    sptrsv::SolveConfig cfg;
+    // refinement buffers
+    sptrsv::DevArr<float> d32;
+    sptrsv::DevArr<double> r64;
+    double analyze_ms = 0.0, transform_ms = 0.0;
+    int32_t thin_rows_used = 0;
+    sptrsv_status_t latched = SPTRSV_OK;
+    sptrsv_mlp_t costmodel = nullptr;  // not owned
+    // profiling: events around the main solve kernel of the last solve
+    bool profiling = false;
+    cudaEvent_t prof_ev[2] = {nullptr, nullptr};
+    bool prof_valid = false;
+    ~sptrsv_plan_s() {
+        if (prof_ev[0]) cudaEventDestroy(prof_ev[0]);
+        if (prof_ev[1]) cudaEventDestroy(prof_ev[1]);
+    }
+};

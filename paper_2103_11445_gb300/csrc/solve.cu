@@ -1,0 +1,460 @@
+// Solve kernels over the level-ordered structure built by the transform.
+//
+// Level-set execution (Sec. II): rows of a level run in parallel, levels run
+// in sequence.  Two kernels share one chunk processor:
+//  * solve_barrier_kernel: a persistent, co-resident grid walks the schedule
+//    of phases; a phase is either one level processed by the whole grid, or a
+//    run of consecutive thin levels processed by a single CTA with
+//    __syncthreads between levels (no grid-wide synchronisation inside the
+//    run).  A grid barrier separates phases.
+//  * solve_syncfree_kernel: the synchronisation-free alternative of Sec. II
+//    (rows wait for their own dependencies only).  Chunks are taken in level
+//    order by a persistent grid; every unknown is pre-set to a signalling-NaN
+//    sentinel and a lane spins (bounded) on the unknowns it reads until they
+//    hold computed values, so the value is its own ready flag and no fence
+//    is needed between producer and consumer.
+// Every lane of a chunk handles one row (L lanes per row for long rows,
+// summed by shuffles) or, with several right-hand sides, one (row, column).
+#include "solve.cuh"
+
+namespace sptrsv {
+namespace {
+
+template <typename T> struct Bits;
+template <> struct Bits<double> {
+    using U = unsigned long long;
+    static __device__ __forceinline__ U load(const double *p) { return ld_relaxed_u64(p); }
+    static __device__ __forceinline__ void store(double *p, double v) {
+        U b = (U)__double_as_longlong(v);
+        if (b == Sentinel<double>::bits) b = 0x7FF8000000000000ull;
+        st_relaxed_u64(p, b);
+    }
+    static __device__ __forceinline__ double from(U b) { return __longlong_as_double((long long)b); }
+    static __device__ __forceinline__ U of(double v) { return (U)__double_as_longlong(v); }
+};
+template <> struct Bits<float> {
+    using U = unsigned;
+    static __device__ __forceinline__ U load(const float *p) { return ld_relaxed_u32(p); }
+    static __device__ __forceinline__ void store(float *p, float v) {
+        U b = __float_as_uint(v);
+        if (b == Sentinel<float>::bits) b = 0x7FC00000u;
+        st_relaxed_u32(p, b);
+    }
+    static __device__ __forceinline__ float from(U b) { return __uint_as_float(b); }
+    static __device__ __forceinline__ U of(float v) { return __float_as_uint(v); }
+};
+
+// Value of an unknown written by another warp of this launch.
+template <typename T, bool SF>
+__device__ __forceinline__ T load_x(const T *p) {
+    if (SF) return Bits<T>::from(Bits<T>::load(p));
+    return __ldcg(p);
+}
+
+// Bounded spin until *p holds a computed value (synchronisation-free only).
+template <typename T>
+__device__ __noinline__ T wait_x(const T *p, DevStatus *st, uint64_t timeout_ns, bool &bail) {
+    WaitBudget wb(timeout_ns);
+    unsigned it = 0;
+    typename Bits<T>::U b;
+    do {
+        if ((++it & kPollMask) == 0 && wb.expired(st, -2)) { bail = true; return T(0); }
+        b = Bits<T>::load(p);
+    } while (b == Sentinel<T>::bits);
+    return Bits<T>::from(b);
+}
+
+template <typename T, bool SF>
+__device__ __forceinline__ void store_x(T *p, T v) {
+    if (SF) Bits<T>::store(p, v);
+    else *p = v;
+}
+
+struct Ctx {
+    const double *rhs;
+    int ld;
+    int nr;
+    DevStatus *st;
+    uint64_t timeout_ns;
+};
+
+// One right-hand side; L lanes per row (compile time).
+template <typename T, int L, bool SF>
+__device__ __forceinline__ bool chunk_one(const SolveData<T> &sd, int32_t c, T *out,
+                                          const Ctx &cx) {
+    const int lane = threadIdx.x & 31;
+    const int k = lane / L, s = lane % L;
+    const int4 mt = __ldg(&sd.meta[c]);
+    const bool active = k < mt.y;
+    T acc = T(0);
+    bool bail = false;
+    if (active) {
+        const int64_t stride = (int64_t)mt.y * L;
+        const int32_t *cp = sd.ecol + mt.w + k * L + s;
+        const T *vp = sd.eval + mt.w + k * L + s;
+        int step = 0;
+        constexpr int U = 4;
+        for (; step + U <= mt.z; step += U) {
+            int32_t cc[U];
+            T vv[U], xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                cc[u] = __ldg(cp + (int64_t)(step + u) * stride);
+                vv[u] = __ldg(vp + (int64_t)(step + u) * stride);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (cc[u] >= 0) xv[u] = load_x<T, SF>(out + (int64_t)cc[u] * cx.ld);
+                else if (cc[u] != PAD_COL) xv[u] = (T)__ldg(cx.rhs + (int64_t)(~cc[u]) * cx.ld);
+                else xv[u] = T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (SF && cc[u] >= 0 && Bits<T>::of(xv[u]) == Sentinel<T>::bits)
+                    xv[u] = wait_x<T>(out + (int64_t)cc[u] * cx.ld, cx.st, cx.timeout_ns, bail);
+                acc = fma(vv[u], xv[u], acc);
+            }
+        }
+        for (; step < mt.z; ++step) {
+            const int32_t cc = __ldg(cp + (int64_t)step * stride);
+            const T v = __ldg(vp + (int64_t)step * stride);
+            T xv = T(0);
+            if (cc >= 0) {
+                xv = load_x<T, SF>(out + (int64_t)cc * cx.ld);
+                if (SF && Bits<T>::of(xv) == Sentinel<T>::bits)
+                    xv = wait_x<T>(out + (int64_t)cc * cx.ld, cx.st, cx.timeout_ns, bail);
+            } else if (cc != PAD_COL) {
+                xv = (T)__ldg(cx.rhs + (int64_t)(~cc) * cx.ld);
+            }
+            acc = fma(v, xv, acc);
+        }
+    }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
+    if (active && s == 0) {
+        const int32_t p = mt.x + k;
+        const int32_t r = __ldg(&sd.row_id[p]);
+        const T res = ((T)__ldg(cx.rhs + (int64_t)r * cx.ld) - acc) / __ldg(&sd.diag[p]);
+        store_x<T, SF>(out + (int64_t)r * cx.ld, res);
+    }
+    return __any_sync(FULL_MASK, bail);
+}
+
+// Several right-hand sides: R lanes per row, lane r owns column r.
+template <typename T, int R, bool SF>
+__device__ __forceinline__ bool chunk_multi(const SolveData<T> &sd, int32_t c, T *out,
+                                            const Ctx &cx) {
+    constexpr int G = 32 / R;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / R, r = lane % R;
+    const int4 mt = __ldg(&sd.meta[c]);
+    const int L = sd.L;
+    const int64_t stride = (int64_t)mt.y * L;
+    bool bail = false;
+    for (int kb = 0; kb < mt.y; kb += G) {
+        const int k = kb + g;
+        const bool rowok = k < mt.y;
+        const bool active = rowok && r < cx.nr;
+        T acc = T(0);
+        if (rowok) {
+            const int64_t base = mt.w + (int64_t)k * L;
+            for (int step = 0; step < mt.z; ++step) {
+                for (int sub = 0; sub < L; ++sub) {
+                    const int64_t slot = base + (int64_t)step * stride + sub;
+                    const int32_t cc = __ldg(sd.ecol + slot);
+                    if (cc == PAD_COL || !active) continue;
+                    const T v = __ldg(sd.eval + slot);
+                    T xv;
+                    if (cc >= 0) {
+                        T *px = out + (int64_t)cc * cx.ld + r;
+                        xv = load_x<T, SF>(px);
+                        if (SF && Bits<T>::of(xv) == Sentinel<T>::bits)
+                            xv = wait_x<T>(px, cx.st, cx.timeout_ns, bail);
+                    } else {
+                        xv = (T)__ldg(cx.rhs + (int64_t)(~cc) * cx.ld + r);
+                    }
+                    acc = fma(v, xv, acc);
+                }
+            }
+        }
+        if (active) {
+            const int32_t p = mt.x + k;
+            const int32_t row = __ldg(&sd.row_id[p]);
+            const T res = ((T)__ldg(cx.rhs + (int64_t)row * cx.ld + r) - acc) / __ldg(&sd.diag[p]);
+            store_x<T, SF>(out + (int64_t)row * cx.ld + r, res);
+        }
+        if (__any_sync(FULL_MASK, bail)) return true;
+    }
+    return false;
+}
+
+template <typename T, int L, int R, bool SF>
+__device__ __forceinline__ bool process_chunk(const SolveData<T> &sd, int32_t c, T *out,
+                                              const Ctx &cx) {
+    if (R == 1) return chunk_one<T, L, SF>(sd, c, out, cx);
+    return chunk_multi<T, R, SF>(sd, c, out, cx);
+}
+
+__device__ __forceinline__ bool converged(const DevStatus *st) {
+    return ld_relaxed_u64(&st->ir_flag) != 0ull;
+}
+
+template <typename T, int L, int R>
+__global__ void __launch_bounds__(1024)
+solve_barrier_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr,
+                     DevStatus *st, uint64_t timeout_ns, int skip_if_converged) {
+    if (skip_if_converged && converged(st)) return;  // uniform: set by an earlier kernel
+    const Ctx cx{rhs, ld, nr, st, timeout_ns};
+    const int wpb = blockDim.x >> 5, wib = threadIdx.x >> 5;
+    const int32_t gw = blockIdx.x * wpb + wib;
+    const int32_t nw = gridDim.x * wpb;
+    unsigned long long bar = 0;
+    for (int ph = 0; ph < sd.nphases; ++ph) {
+        const int2 p = __ldg(&sd.phases[ph]);
+        if (p.y > 0) {
+            const int32_t c1 = __ldg(&sd.lvl_chunk[p.x + 1]);
+            for (int32_t c = __ldg(&sd.lvl_chunk[p.x]) + gw; c < c1; c += nw)
+                process_chunk<T, L, R, false>(sd, c, out, cx);
+        } else if ((int)blockIdx.x == ph % (int)gridDim.x) {
+            for (int32_t l = p.x; l < -p.y; ++l) {
+                const int32_t c1 = __ldg(&sd.lvl_chunk[l + 1]);
+                for (int32_t c = __ldg(&sd.lvl_chunk[l]) + wib; c < c1; c += wpb)
+                    process_chunk<T, L, R, false>(sd, c, out, cx);
+                __syncthreads();
+            }
+        }
+        if (ph + 1 < sd.nphases && !grid_barrier(st, (++bar) * gridDim.x, timeout_ns, ph))
+            break;
+    }
+    grid_exit(st);
+}
+
+template <typename T, int L, int R>
+__global__ void __launch_bounds__(1024)
+solve_syncfree_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr,
+                      DevStatus *st, uint64_t timeout_ns, int skip_if_converged) {
+    if (skip_if_converged && converged(st)) return;
+    const Ctx cx{rhs, ld, nr, st, timeout_ns};
+    const int wpb = blockDim.x >> 5;
+    const int32_t gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+    const int32_t nw = gridDim.x * wpb;
+    // Chunks are taken in level order, each warp its own arithmetic sequence:
+    // with every warp resident, the lowest unfinished chunk's warp has
+    // finished its earlier chunks and all that chunk's dependencies lie in
+    // earlier levels, so some warp can always make progress.
+    for (int32_t c = gw; c < sd.nchunks; c += nw)
+        if (process_chunk<T, L, R, true>(sd, c, out, cx)) break;
+}
+
+template <typename T>
+__global__ void fill_sentinel(T *out, int32_t n, int ld, int nr, DevStatus *st,
+                              int skip_if_converged) {
+    if (skip_if_converged && converged(st)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)n * nr;
+    if (i >= total) return;
+    const int64_t row = i / nr, c = i % nr;
+    *reinterpret_cast<typename Bits<T>::U *>(out + row * ld + c) = Sentinel<T>::bits;
+}
+
+template <typename T, bool SF, int R>
+const void *pick_l(int L) {
+    if (R > 1) {
+        return SF ? (const void *)solve_syncfree_kernel<T, 1, R>
+                  : (const void *)solve_barrier_kernel<T, 1, R>;
+    }
+    switch (L) {
+#define SPTRSV_CASE(LL)                                                        \
+    case LL:                                                                   \
+        return SF ? (const void *)solve_syncfree_kernel<T, LL, 1>              \
+                  : (const void *)solve_barrier_kernel<T, LL, 1>;
+        SPTRSV_CASE(1) SPTRSV_CASE(2) SPTRSV_CASE(4) SPTRSV_CASE(8) SPTRSV_CASE(16)
+        SPTRSV_CASE(32)
+#undef SPTRSV_CASE
+    }
+    return nullptr;
+}
+
+template <typename T, bool SF>
+const void *pick(int L, int nr) {
+    if (nr <= 1) return pick_l<T, SF, 1>(L);
+    if (nr <= 2) return pick_l<T, SF, 2>(L);
+    if (nr <= 4) return pick_l<T, SF, 4>(L);
+    if (nr <= 8) return pick_l<T, SF, 8>(L);
+    if (nr <= 16) return pick_l<T, SF, 16>(L);
+    return pick_l<T, SF, 32>(L);
+}
+
+template <typename T>
+const void *pick_kernel(int L, int nr, bool syncfree) {
+    return syncfree ? pick<T, true>(L, nr) : pick<T, false>(L, nr);
+}
+
+// ---------------------------------------------------------------------------
+// Refinement kernels (FP64 residual of the original L, FP32 corrections).
+
+__global__ void residual_kernel(int32_t n, const int32_t *__restrict__ row_ptr,
+                                const int32_t *__restrict__ col,
+                                const double *__restrict__ val, const double *__restrict__ b,
+                                const double *__restrict__ x, double *__restrict__ r, int nr,
+                                int ld, DevStatus *st) {
+    if (converged(st)) return;
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    double rmax = 0.0, xmax = 0.0;
+    if (i < n) {
+        const int32_t a = row_ptr[i], e = row_ptr[i + 1];
+        for (int c = 0; c < nr; ++c) {
+            double s = b[(int64_t)i * ld + c];
+            for (int32_t k = a; k < e; ++k) s -= val[k] * x[(int64_t)col[k] * ld + c];
+            r[(int64_t)i * ld + c] = s;
+            rmax = fmax(rmax, fabs(s));
+            xmax = fmax(xmax, fabs(x[(int64_t)i * ld + c]));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rmax = fmax(rmax, __shfl_xor_sync(FULL_MASK, rmax, o));
+        xmax = fmax(xmax, __shfl_xor_sync(FULL_MASK, xmax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        unsigned long long *nm = reinterpret_cast<unsigned long long *>(st->norms);
+        atomicMax(&nm[0], (unsigned long long)__double_as_longlong(rmax));
+        atomicMax(&nm[1], (unsigned long long)__double_as_longlong(xmax));
+    }
+}
+
+__global__ void ir_bnorm_kernel(DevStatus *st, const double *__restrict__ b, int64_t count) {
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(b[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(FULL_MASK, m, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(reinterpret_cast<unsigned long long *>(&st->norms[2]),
+                  (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void ir_decide_kernel(DevStatus *st, double tol, const unsigned long long *lnorm) {
+    unsigned long long *nm = reinterpret_cast<unsigned long long *>(st->norms);
+    if (st->ir_flag) return;
+    const double rn = __longlong_as_double((long long)nm[0]);
+    const double xn = __longlong_as_double((long long)nm[1]);
+    const double bn = __longlong_as_double((long long)nm[2]);
+    const double ln = __longlong_as_double((long long)*lnorm);
+    if (rn <= tol * (ln * xn + bn)) st->ir_flag = 1ull;
+    else st->ir_iters += 1;
+    nm[0] = 0ull;
+    nm[1] = 0ull;
+}
+
+__global__ void ir_update_kernel(double *__restrict__ x, const float *__restrict__ d,
+                                 int64_t count, int first, DevStatus *st) {
+    if (!first && converged(st)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    x[i] = first ? (double)d[i] : x[i] + (double)d[i];
+}
+
+}  // namespace
+
+template <typename T>
+int max_coresident_ctas(int L, int nr, bool syncfree, int block_threads, int num_sms) {
+    const void *k = pick_kernel<T>(L, nr, syncfree);
+    if (!k) return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block_threads, 0) !=
+        cudaSuccess)
+        return 0;
+    return per_sm * num_sms;
+}
+template int max_coresident_ctas<double>(int, int, bool, int, int);
+template int max_coresident_ctas<float>(int, int, bool, int, int);
+
+template <typename T>
+cudaError_t launch_fill_sentinel(T *out, int32_t n, int ld, int nr, DevStatus *st,
+                                 bool skip_if_converged, cudaStream_t s) {
+    const int64_t total = (int64_t)n * nr;
+    if (total == 0) return cudaSuccess;
+    fill_sentinel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(out, n, ld, nr, st,
+                                                                     skip_if_converged ? 1 : 0);
+    return cudaGetLastError();
+}
+template cudaError_t launch_fill_sentinel<double>(double *, int32_t, int, int, DevStatus *, bool,
+                                                  cudaStream_t);
+template cudaError_t launch_fill_sentinel<float>(float *, int32_t, int, int, DevStatus *, bool,
+                                                 cudaStream_t);
+
+template <typename T>
+cudaError_t launch_solve(const SolveData<T> &sd, const double *rhs, T *out, int32_t n,
+                         int ld, int nr, bool syncfree, const LaunchCfg &cfg,
+                         DevStatus *st, uint64_t timeout_ns, bool skip_if_converged,
+                         cudaStream_t s, bool prefilled) {
+    if (n == 0 || nr == 0) return cudaSuccess;
+    const void *k = pick_kernel<T>(sd.L, nr, syncfree);
+    if (!k) return cudaErrorInvalidValue;
+    const int skip = skip_if_converged ? 1 : 0;
+    if (syncfree && !prefilled) {
+        cudaError_t e = launch_fill_sentinel<T>(out, n, ld, nr, st, skip_if_converged, s);
+        if (e != cudaSuccess) return e;
+    }
+    SolveData<T> sdc = sd;
+    void *args[] = {(void *)&sdc, (void *)&rhs,        (void *)&out,  (void *)&ld,
+                    (void *)&nr,  (void *)&st,         (void *)&timeout_ns,
+                    (void *)&skip};
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(cfg.grid);
+    lc.blockDim = dim3(cfg.block_threads);
+    lc.dynamicSmemBytes = 0;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelExC(&lc, k, args);
+}
+template cudaError_t launch_solve<double>(const SolveData<double> &, const double *, double *,
+                                          int32_t, int, int, bool, const LaunchCfg &,
+                                          DevStatus *, uint64_t, bool, cudaStream_t, bool);
+template cudaError_t launch_solve<float>(const SolveData<float> &, const double *, float *,
+                                         int32_t, int, int, bool, const LaunchCfg &,
+                                         DevStatus *, uint64_t, bool, cudaStream_t, bool);
+
+cudaError_t launch_residual(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                            const double *val, const double *b, const double *x, double *r,
+                            int nr, int ld, DevStatus *st, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    residual_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, row_ptr, col, val, b, x, r, nr, ld, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ir_begin(DevStatus *st, const double *b, int64_t count, cudaStream_t s) {
+    // reset ir_iters (int at offset 12) and ir_flag + norms
+    cudaError_t e = cudaMemsetAsync(&st->ir_iters, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(&st->ir_flag, 0, sizeof(unsigned long long) + sizeof(st->norms), s);
+    if (e != cudaSuccess) return e;
+    if (count > 0) {
+        int64_t blocks = (count + 255) / 256;
+        if (blocks > 4096) blocks = 4096;
+        ir_bnorm_kernel<<<(unsigned)blocks, 256, 0, s>>>(st, b, count);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ir_decide(DevStatus *st, double tol, const unsigned long long *lnorm,
+                             cudaStream_t s) {
+    ir_decide_kernel<<<1, 1, 0, s>>>(st, tol, lnorm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ir_update(double *x, const float *d, int64_t count, bool first,
+                             DevStatus *st, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    ir_update_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(x, d, count, first ? 1 : 0,
+                                                                    st);
+    return cudaGetLastError();
+}
+
+}  // namespace sptrsv

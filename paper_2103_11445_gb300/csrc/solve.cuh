@@ -1,0 +1,68 @@
+// Solve kernels (solve.cu): structure of the level-ordered solve data and the
+// launchers.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace sptrsv {
+
+// Level-ordered solve structure (device pointers).  Rows are stored in solve
+// order (level by level); each level is cut into chunks of H = 32 / L rows.
+// Chunk c: meta[c] = (first solve position, rows, width, entry offset).
+// Entry j of row k of the chunk sits at
+//     off + (j / L) * (rows * L) + k * L + (j % L)
+// so the chunk's active lanes read consecutive words every step.  ecol >= 0
+// is an x term, ecol < 0 (not PAD_COL) a b term of a rewritten row.
+template <typename T>
+struct SolveData {
+    int32_t nlev;
+    int32_t nchunks;
+    int32_t L;                  // lanes per row of the layout
+    const int32_t *lvl_chunk;   // [nlev + 1]
+    const int4 *meta;           // [nchunks]
+    const int32_t *ecol;
+    const T *eval;
+    const int32_t *row_id;      // solve position -> row
+    const T *diag;              // solve position -> L_ii
+    const int2 *phases;         // barrier schedule: (l0, l1) level, or (l0, -l1) CTA-local run
+    int32_t nphases;
+};
+
+struct LaunchCfg {
+    int block_threads;   // threads per CTA
+    int grid;            // CTAs (co-resident)
+};
+
+// x = L^{-1} rhs for `nr` right-hand sides stored with leading dimension ld
+// (row i, column r at [i * ld + r]).  rhs is FP64; out has type T.
+// syncfree selects the synchronisation-free kernel (out is pre-filled with
+// the sentinel by this launcher).  `skip_if_converged`: the kernels return
+// at once when st->ir_flag is set (refinement loop).
+template <typename T>
+cudaError_t launch_solve(const SolveData<T> &sd, const double *rhs, T *out, int32_t n,
+                         int ld, int nr, bool syncfree, const LaunchCfg &cfg,
+                         DevStatus *st, uint64_t timeout_ns, bool skip_if_converged,
+                         cudaStream_t s, bool prefilled = false);
+// Sentinel pre-fill of the synchronisation-free solve's output.
+template <typename T>
+cudaError_t launch_fill_sentinel(T *out, int32_t n, int ld, int nr, DevStatus *st,
+                                 bool skip_if_converged, cudaStream_t s);
+
+// Largest co-resident grid for the chosen kernel (CTAs per SM * SMs).
+template <typename T>
+int max_coresident_ctas(int L, int nr, bool syncfree, int block_threads, int num_sms);
+
+// FP64 residual r = b - L x over the original CSR, with infinity norms of r
+// and x accumulated in st->norms[0], [1]; returns at once when ir_flag is set.
+cudaError_t launch_residual(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                            const double *val, const double *b, const double *x, double *r,
+                            int nr, int ld, DevStatus *st, cudaStream_t s);
+// Refinement bookkeeping.
+cudaError_t launch_ir_begin(DevStatus *st, const double *b, int64_t count, cudaStream_t s);
+cudaError_t launch_ir_decide(DevStatus *st, double tol, const unsigned long long *lnorm,
+                             cudaStream_t s);
+// x = (double) d (first step), or x += d (later steps, skipped when converged)
+cudaError_t launch_ir_update(double *x, const float *d, int64_t count, bool first,
+                             DevStatus *st, cudaStream_t s);
+
+}  // namespace sptrsv

@@ -1,0 +1,50 @@
+// Launchers of the rewriting and assembly kernels (transform.cu).
+#pragma once
+
+#include "kernels.cuh"
+
+namespace sptrsv {
+
+cudaError_t launch_expand_queries(int32_t nq, const int32_t *q_level, const int32_t *q_tgt,
+                                  const int64_t *q_off, const int32_t *level_ptr,
+                                  const int32_t *perm, int32_t *item_row, int32_t *item_tgt,
+                                  int32_t *item_q, int32_t *item_pos, cudaStream_t s);
+cudaError_t launch_rewrite_count(int64_t nitems, const int32_t *item_row,
+                                 const int32_t *item_tgt, const int32_t *item_q,
+                                 const int32_t *row_ptr, const int32_t *col,
+                                 const int32_t *level, int cap, int32_t *fill_out,
+                                 unsigned long long *added, int32_t *overflow,
+                                 int num_sms, cudaStream_t s);
+cudaError_t launch_rewrite_numeric(int64_t nitems, const int32_t *item_row,
+                                   const int32_t *item_tgt, const int64_t *out_off,
+                                   const int32_t *row_ptr, const int32_t *col,
+                                   const double *val, const int32_t *level, int cap,
+                                   int32_t *out_col, double *out_val, int32_t *nb_out,
+                                   DevStatus *st, int num_sms, cudaStream_t s);
+cudaError_t launch_pos_item(int32_t n, int64_t nitems, const int32_t *item_pos,
+                            int32_t *pos_item, cudaStream_t s);
+cudaError_t launch_chunk_width(int32_t nchunks, const int32_t *c_row0, const int32_t *c_nrows,
+                               int L, const int32_t *perm, const int32_t *offdeg,
+                               const int32_t *pos_item, const int64_t *rw_off, int64_t *slots,
+                               int32_t *width, cudaStream_t s);
+template <typename T>
+cudaError_t launch_chunk_fill(int32_t nchunks, int L, const int32_t *c_row0,
+                              const int32_t *c_nrows, const int32_t *c_width,
+                              const int64_t *c_off, const int32_t *perm, const int32_t *row_ptr,
+                              const int32_t *col, const double *val, const int32_t *pos_item,
+                              const int64_t *rw_off, const int32_t *rw_col,
+                              const double *rw_val, int4 *meta, int32_t *ecol, T *eval,
+                              int32_t *row_id, T *diag, cudaStream_t s);
+cudaError_t launch_export_count(int32_t nchunks, int L, const int4 *meta, const int32_t *ecol,
+                                const int32_t *row_id, int64_t *xcnt, int64_t *bcnt,
+                                cudaStream_t s);
+cudaError_t launch_export_fill(int32_t nchunks, int L, const int4 *meta, const int32_t *ecol,
+                               const double *eval, const int32_t *row_id,
+                               const int32_t *chunk_level, const int64_t *xptr,
+                               const int64_t *bptr, int32_t *xcol, double *xval,
+                               int32_t *bcol, double *bw, int32_t *new_level, cudaStream_t s);
+cudaError_t launch_chunk_level(int32_t nlev, const int32_t *lvl_chunk, int32_t *chunk_level,
+                               cudaStream_t s);
+cudaError_t launch_f64_to_f32(const double *a, float *b, int64_t n, cudaStream_t s);
+
+}  // namespace sptrsv
