@@ -49,6 +49,15 @@ def parse():
     ap.add_argument("--depths", default="1,2,3,4,6",
                     help="fixed rewrite depths tried besides heuristic H")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--profile-run", action="store_true",
+                    help="no search, no CPU leg, no e2e: analyze, one transform with the "
+                         "given --select/--mode/--lanes/--block, then warmup + steps solves "
+                         "(the command the ncu captures use)")
+    ap.add_argument("--select", default="fixed_d2",
+                    help="profile-run selection: plain, heuristic or fixed_d<k>")
+    ap.add_argument("--mode", choices=["barrier", "syncfree"], default="syncfree")
+    ap.add_argument("--lanes", type=int, default=4)
+    ap.add_argument("--block", type=int, default=256)
     return ap.parse_args()
 
 
@@ -231,6 +240,47 @@ def run_reference(args, world, rank):
     return 0
 
 
+def select_kw(name: str, Bd) -> dict:
+    if name == "plain":
+        return dict(select_mode=Bd.SELECT_NONE)
+    if name == "heuristic":
+        return dict(select_mode=Bd.SELECT_HEURISTIC)
+    if name.startswith("fixed_d"):
+        return dict(select_mode=Bd.SELECT_FIXED, depth=int(name[len("fixed_d"):]))
+    raise ValueError(name)
+
+
+def run_profile(args):
+    """Fixed configuration, no autotuning: the command ncu captures."""
+    import torch
+    from paper_2103_11445_gb300 import binding as Bd
+    dev = torch.device("cuda", torch.cuda.current_device())
+    A, b_np = workload(args.side)
+    P = Bd.Plan(A.n, A.row_ptr, A.col, A.val)
+    mode = Bd.SOLVE_SYNCFREE if args.mode == "syncfree" else Bd.SOLVE_BARRIER
+    P.transform(solve_mode=mode, lanes_per_row=args.lanes, block_threads=args.block,
+                cta_run_rows=-1, **select_kw(args.select, Bd))
+    b = torch.as_tensor(b_np, device=dev)
+    x = torch.empty_like(b)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    times = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        P.solve(b, x)
+        e1.record()
+        e1.synchronize()
+        if k >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+    P.check()
+    info = P.info()
+    print(json.dumps({"profile_run": args.select, "mode": args.mode, "ms": times,
+                      "levels_after": info["nlev_new"], "L": info["lanes_per_row"],
+                      "grid": info["grid_blocks"], "block": info["block_threads"]}))
+    return 0
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -306,11 +356,6 @@ def run_ours(args, world, rank, local):
         barrier(world)
         return info, step_ms, kern_ms
 
-    # plain level-set, same protocol
-    pinfo, p_steps, p_kern = measure(results["plain"]["kw"], args.steps, args.warmup, "plain")
-    plain_ms = max_over_ranks(world, statistics.mean(p_steps))
-
-    # headline: rewritten, autotuned
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(dev).uuid)
@@ -318,6 +363,11 @@ def run_ours(args, world, rank, local):
         pass
     clocks = ClockSampler(uuid)
     clocks.start()
+    # plain level-set, same protocol
+    pinfo, p_steps, p_kern = measure(results["plain"]["kw"], args.steps, args.warmup, "plain")
+    plain_ms = max_over_ranks(world, statistics.mean(p_steps))
+
+    # headline: rewritten, autotuned
     info, steps_ms, kern_ms = measure(rewritten[best]["kw"], args.steps, args.warmup, best)
     clk = clocks.stop()
     ms = max_over_ranks(world, statistics.mean(steps_ms))
@@ -411,6 +461,8 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         rc = run_reference(args, world, rank)
+    elif args.profile_run:
+        rc = run_profile(args)
     else:
         rc = run_ours(args, world, rank, local)
     if world > 1:
