@@ -192,6 +192,30 @@ SPTRSV_API sptrsv_status_t sptrsv_get_transformed(sptrsv_plan_t p, int32_t *d_ne
                                        int32_t *d_bcol, double *d_bw,
                                        sptrsv_stream_t stream);
 
+/* The FP32 + FP64-refinement solve without any device allocation.  The
+ * paper has no counterpart: this exists for callers that cannot call
+ * cudaMalloc when they solve -- code recording a CUDA graph, applications
+ * whose device memory comes from their own pool or is fixed at start-up,
+ * loops that must not synchronise the device.  sptrsv_solve in SPTRSV_F32_IR
+ * precision allocates its two scratch arrays (FP32 correction, FP64
+ * residual) on first use of a size; this call takes them instead from one
+ * file-scope __device__ array of 12 MiB that every GPU loading the library
+ * holds until the process exits.
+ *  - The plan must have been transformed with precision SPTRSV_F32_IR
+ *    (SPTRSV_ERR_BAD_STATE otherwise); b and x as for sptrsv_solve.
+ *  - n * nrhs must not exceed 1,048,576 (SPTRSV_ERR_UNSUPPORTED otherwise).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) once; make that first call before any stream
+ *    capture.
+ *  - All calls, on every plan and stream, share the one array: calls that
+ *    overlap on the GPU race and give wrong results.  Nothing in it needs to
+ *    start at zero; it keeps whatever the last call left.
+ *  - Asynchronous like sptrsv_solve; errors found by kernels are latched in
+ *    the plan and returned by sptrsv_check. */
+SPTRSV_API sptrsv_status_t sptrsv_solve_ir_noalloc(sptrsv_plan_t p, const double *d_b,
+                                                   double *d_x, int32_t nrhs,
+                                                   sptrsv_stream_t stream);
+
 /* Profiling (not part of the paper's method): while enabled, sptrsv_solve
  * records CUDA events on its stream around its main solve kernel(s) (after
  * the sentinel pre-fill of the synchronisation-free variant; FP64 only).

@@ -85,6 +85,7 @@ _SIGS = {
                                          c_void_p]),
     "sptrsv_debug_inject_wait": (c_int32, [c_void_p, c_int32]),
     "sptrsv_set_profiling": (c_int32, [c_void_p, c_int32]),
+    "sptrsv_solve_ir_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "sptrsv_last_kernel_ms": (c_int32, [c_void_p, POINTER(ctypes.c_float)]),
 }
 
@@ -189,6 +190,12 @@ def sptrsv_get_transformed(plan: int, d_new_level: int, d_xptr: int, d_xcol: int
 
 def sptrsv_debug_inject_wait(plan: int, row: int) -> None:
     _check(load().sptrsv_debug_inject_wait(plan, row), "sptrsv_debug_inject_wait")
+
+
+def sptrsv_solve_ir_noalloc(plan: int, d_b: int, d_x: int, nrhs: int,
+                            stream: int = 0) -> None:
+    _check(load().sptrsv_solve_ir_noalloc(plan, d_b, d_x, nrhs, stream),
+           "sptrsv_solve_ir_noalloc")
 
 
 def sptrsv_set_profiling(plan: int, on: bool) -> None:
