@@ -111,6 +111,11 @@ typedef struct {
                                 one CTA (no grid barrier); 0 = auto, <0 = off */
     int32_t wait_timeout_ms; /* bound on every device wait (default 5000); a
                                 solve longer than this is reported as TIMEOUT */
+    int32_t grid_blocks;     /* CTAs of the persistent solve (clipped to the
+                                co-resident maximum); 0 = auto */
+    int32_t poll_backoff_ns; /* synchronisation-free solve: sleep between
+                                polls of an unready unknown; 0 = none,
+                                < 0 = auto */
 } sptrsv_transform_params_t;
 
 /* Everything a caller may want to report about a plan. */
@@ -131,6 +136,7 @@ typedef struct {
     int32_t ir_iters_last;   /* refinement steps of the last F32_IR solve
                                 (valid after a synchronisation) */
     int32_t num_sms;
+    int32_t poll_backoff_ns;
     double analyze_ms, transform_ms;
 } sptrsv_info_t;
 

@@ -468,9 +468,25 @@ sptrsv_status_t autotune(sptrsv_plan_t p, cudaStream_t s) {
             c.L = L;
             c.syncfree = mode == 2;
             c.block_threads = bt_req > 0 ? bt_req : 512;
-            c.grid = c.syncfree ? 0 : p->num_sms;
+            c.grid = p->prm.grid_blocks > 0 ? p->prm.grid_blocks : (c.syncfree ? 0 : p->num_sms);
+            c.backoff_ns = p->prm.poll_backoff_ns > 0 ? p->prm.poll_backoff_ns : 0;
             c.cta_run_rows = mode == 1 ? c.block_threads / L : 0;
             if (p->prm.cta_run_rows < 0 && mode == 1) continue;
+            p->cfg = c;
+            double ms;
+            CKS(time_cfg(&ms));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+    }
+    // polling back-off of the synchronisation-free kernel
+    if (best.syncfree && p->prm.poll_backoff_ns < 0) {
+        const SolveConfig b0 = best;
+        for (int ns : {32, 128, 512}) {
+            SolveConfig c = b0;
+            c.backoff_ns = ns;
             p->cfg = c;
             double ms;
             CKS(time_cfg(&ms));
@@ -534,7 +550,8 @@ sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t 
     const int32_t n = p->n;
     const uint64_t tmo = timeout_ns(p);
     if (p->prm.precision != SPTRSV_F32_IR) {
-        const SolveData<double> sd = p->s64.view();
+        SolveData<double> sd = p->s64.view();
+        sd.backoff_ns = p->cfg.backoff_ns;
         if (p->cfg.syncfree) {
             // sentinel pre-fill first, so the events bracket the solve kernel alone
             for (int32_t c0 = 0; c0 < nrhs; c0 += 32)
@@ -559,7 +576,8 @@ sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t 
     // FP32 solve with FP64 iterative refinement
     const int64_t count = (int64_t)n * nrhs;
     CKS(ensure_ir(p, count));
-    const SolveData<float> sd = p->s32.view();
+    SolveData<float> sd = p->s32.view();
+    sd.backoff_ns = p->cfg.backoff_ns;
     auto solve32 = [&](const double *rhs, bool skip) -> sptrsv_status_t {
         for (int32_t c0 = 0; c0 < nrhs; c0 += 32) {
             const int nr = std::min<int32_t>(32, nrhs - c0);
@@ -621,6 +639,8 @@ void sptrsv_default_params(sptrsv_transform_params_t *prm) {
     prm->block_threads = 0;
     prm->cta_run_rows = 0;
     prm->wait_timeout_ms = 5000;
+    prm->grid_blocks = 0;
+    prm->poll_backoff_ns = -1;
 }
 
 sptrsv_status_t sptrsv_analyze(int32_t n, int64_t nnz, const int32_t *d_row_ptr,
@@ -787,7 +807,8 @@ sptrsv_status_t sptrsv_transform(sptrsv_plan_t p, const sptrsv_transform_params_
     SolveConfig c;
     c.syncfree = p->prm.solve_mode == SPTRSV_SOLVE_SYNCFREE;
     c.block_threads = p->prm.block_threads > 0 ? p->prm.block_threads : 512;
-    c.grid = c.syncfree ? 0 : p->num_sms;
+    c.grid = p->prm.grid_blocks > 0 ? p->prm.grid_blocks : (c.syncfree ? 0 : p->num_sms);
+    c.backoff_ns = p->prm.poll_backoff_ns > 0 ? p->prm.poll_backoff_ns : 0;
     c.L = 1;
     p->cfg = c;
     CKS(build_struct<double>(p, p->s64, 1, s));
@@ -847,6 +868,7 @@ sptrsv_status_t sptrsv_get_info(sptrsv_plan_t p, sptrsv_info_t *o) {
     o->max_depth = p->prm.max_depth;
     o->flop_budget = p->prm.flop_budget;
     o->num_sms = p->num_sms;
+    o->poll_backoff_ns = p->cfg.backoff_ns;
     o->analyze_ms = p->analyze_ms;
     o->transform_ms = p->transform_ms;
     if (p->status.p) {

@@ -84,7 +84,8 @@ extern "C" SPTRSV_API sptrsv_status_t sptrsv_solve_ir_noalloc(sptrsv_plan_t p, c
     const uint64_t tmo = (uint64_t)(p->prm.wait_timeout_ms > 0 ? p->prm.wait_timeout_ms : 5000) *
                          1000000ull;
     const SolveConfig &c = p->cfg;
-    const SolveData<float> sd = p->s32.view();
+    SolveData<float> sd = p->s32.view();
+    sd.backoff_ns = c.backoff_ns;
     auto solve32 = [&](const double *rhs, bool skip) -> cudaError_t {
         for (int32_t c0 = 0; c0 < nrhs; c0 += 32) {
             const int nr = nrhs - c0 < 32 ? nrhs - c0 : 32;

@@ -71,6 +71,7 @@ struct SolveStruct {
         v.diag = diag.p;
         v.phases = phases.p;
         v.nphases = nphases;
+        v.backoff_ns = 0;
         return v;
     }
 };
@@ -81,6 +82,7 @@ struct SolveConfig {
     int block_threads = 512;
     int grid = 0;
     int cta_run_rows = 0;   // resolved threshold (<= 0: no runs)
+    int backoff_ns = 0;     // synchronisation-free polling back-off
 };
 
 }  // namespace sptrsv

@@ -53,15 +53,21 @@ __device__ __forceinline__ T load_x(const T *p) {
 
 // Bounded spin until *p holds a computed value (synchronisation-free only).
 template <typename T>
-__device__ __noinline__ T wait_x(const T *p, DevStatus *st, uint64_t timeout_ns, bool &bail) {
+__device__ __forceinline__ T wait_x_inl(const T *p, DevStatus *st, uint64_t timeout_ns,
+                                        int backoff_ns, bool &bail) {
     WaitBudget wb(timeout_ns);
     unsigned it = 0;
     typename Bits<T>::U b;
     do {
+        if (backoff_ns) __nanosleep(backoff_ns);
         if ((++it & kPollMask) == 0 && wb.expired(st, -2)) { bail = true; return T(0); }
         b = Bits<T>::load(p);
     } while (b == Sentinel<T>::bits);
     return Bits<T>::from(b);
+}
+template <typename T>
+__device__ __noinline__ T wait_x(const T *p, DevStatus *st, uint64_t timeout_ns, bool &bail) {
+    return wait_x_inl<T>(p, st, timeout_ns, 0, bail);
 }
 
 template <typename T, bool SF>
@@ -76,6 +82,7 @@ struct Ctx {
     int nr;
     DevStatus *st;
     uint64_t timeout_ns;
+    int backoff_ns;
 };
 
 // One right-hand side; L lanes per row (compile time).
@@ -188,6 +195,90 @@ __device__ __forceinline__ bool chunk_multi(const SolveData<T> &sd, int32_t c, T
     return false;
 }
 
+
+// ---------------------------------------------------------------------------
+// Software pipeline for one right-hand side: a chunk's entries are loaded
+// into registers (stage_entries) one chunk ahead, so that when the chunk is
+// finished only the gather of its b and x values (one round trip) and the
+// wait for its dependencies remain.  Chunks wider than kPipeSteps entries
+// per lane go through chunk_one.
+constexpr int kPipeSteps = 4;
+
+template <typename T>
+struct Staged {
+    int4 mt;
+    int32_t col[kPipeSteps];
+    T val[kPipeSteps];
+};
+
+__device__ __forceinline__ int4 no_chunk() { return make_int4(0, 0, 0, 0); }
+
+template <typename T, int L>
+__device__ __forceinline__ void stage_entries(const SolveData<T> &sd, Staged<T> &sg) {
+    const int lane = threadIdx.x & 31;
+    const int k = lane / L, s = lane % L;
+    const bool ok = k < sg.mt.y && sg.mt.z <= kPipeSteps;
+    const int64_t stride = (int64_t)sg.mt.y * L;
+    const int64_t base = (int64_t)sg.mt.w + k * L + s;
+#pragma unroll
+    for (int u = 0; u < kPipeSteps; ++u) {
+        if (ok && u < sg.mt.z) {
+            sg.col[u] = __ldg(sd.ecol + base + u * stride);
+            sg.val[u] = __ldg(sd.eval + base + u * stride);
+        } else {
+            sg.col[u] = PAD_COL;
+            sg.val[u] = T(0);
+        }
+    }
+}
+
+template <typename T, int L, bool SF>
+__device__ __forceinline__ bool finish_staged(const SolveData<T> &sd, const Staged<T> &sg,
+                                              T *out, const Ctx &cx) {
+    const int lane = threadIdx.x & 31;
+    const int k = lane / L, s = lane % L;
+    const bool active = k < sg.mt.y;
+    T xv[kPipeSteps];
+#pragma unroll
+    for (int u = 0; u < kPipeSteps; ++u) {
+        const int32_t c = sg.col[u];
+        if (c >= 0) xv[u] = load_x<T, SF>(out + (int64_t)c * cx.ld);
+        else if (c != PAD_COL) xv[u] = (T)__ldg(cx.rhs + (int64_t)(~c) * cx.ld);
+        else xv[u] = T(0);
+    }
+    bool bail = false;
+    T acc = T(0);
+#pragma unroll
+    for (int u = 0; u < kPipeSteps; ++u) {
+        if (SF && sg.col[u] >= 0 && Bits<T>::of(xv[u]) == Sentinel<T>::bits)
+            xv[u] = wait_x_inl<T>(out + (int64_t)sg.col[u] * cx.ld, cx.st, cx.timeout_ns,
+                                  cx.backoff_ns, bail);
+        acc = fma(sg.val[u], xv[u], acc);
+    }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
+    if (active && s == 0) {
+        const int32_t p = sg.mt.x + k;
+        const int32_t r = __ldg(&sd.row_id[p]);
+        const T res = ((T)__ldg(cx.rhs + (int64_t)r * cx.ld) - acc) / __ldg(&sd.diag[p]);
+        store_x<T, SF>(out + (int64_t)r * cx.ld, res);
+    }
+    return __any_sync(FULL_MASK, bail);
+}
+
+template <typename T, int L, bool SF>
+__device__ __forceinline__ bool finish_any(const SolveData<T> &sd, int32_t c,
+                                           const Staged<T> &sg, T *out, const Ctx &cx) {
+    if (sg.mt.z > kPipeSteps) return chunk_one<T, L, SF>(sd, c, out, cx);
+    return finish_staged<T, L, SF>(sd, sg, out, cx);
+}
+
+template <typename T, int L>
+__device__ __forceinline__ void stage_chunk(const SolveData<T> &sd, int32_t c, Staged<T> &sg) {
+    sg.mt = __ldg(&sd.meta[c]);
+    stage_entries<T, L>(sd, sg);
+}
+
 template <typename T, int L, int R, bool SF>
 __device__ __forceinline__ bool process_chunk(const SolveData<T> &sd, int32_t c, T *out,
                                               const Ctx &cx) {
@@ -199,29 +290,66 @@ __device__ __forceinline__ bool converged(const DevStatus *st) {
     return ld_relaxed_u64(&st->ir_flag) != 0ull;
 }
 
+// The warp's first chunk of phase ph (or -1): fat levels are shared by the
+// whole grid, a CTA-local run belongs to CTA ph % gridDim.x.
+template <typename T>
+__device__ __forceinline__ int32_t first_chunk_of_phase(const SolveData<T> &sd, int ph,
+                                                        int32_t gw, int wib) {
+    if (ph >= sd.nphases) return -1;
+    const int2 p = __ldg(&sd.phases[ph]);
+    if (p.y > 0) {
+        const int32_t c = __ldg(&sd.lvl_chunk[p.x]) + gw;
+        return c < __ldg(&sd.lvl_chunk[p.x + 1]) ? c : -1;
+    }
+    if ((int)blockIdx.x != ph % (int)gridDim.x) return -1;
+    const int32_t c = __ldg(&sd.lvl_chunk[p.x]) + wib;
+    return c < __ldg(&sd.lvl_chunk[p.x + 1]) ? c : -1;
+}
+
 template <typename T, int L, int R>
 __global__ void __launch_bounds__(1024)
 solve_barrier_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr,
                      DevStatus *st, uint64_t timeout_ns, int skip_if_converged) {
     if (skip_if_converged && converged(st)) return;  // uniform: set by an earlier kernel
-    const Ctx cx{rhs, ld, nr, st, timeout_ns};
+    const Ctx cx{rhs, ld, nr, st, timeout_ns, 0};
     const int wpb = blockDim.x >> 5, wib = threadIdx.x >> 5;
     const int32_t gw = blockIdx.x * wpb + wib;
     const int32_t nw = gridDim.x * wpb;
     unsigned long long bar = 0;
+    // One right-hand side: the warp's first chunk of the next phase (or of
+    // the next level of a run) is staged before the barrier that precedes it.
+    Staged<T> sg;
+    int32_t staged = -1;
+    if (R == 1) {
+        staged = first_chunk_of_phase<T>(sd, 0, gw, wib);
+        if (staged >= 0) stage_chunk<T, L>(sd, staged, sg);
+    }
     for (int ph = 0; ph < sd.nphases; ++ph) {
         const int2 p = __ldg(&sd.phases[ph]);
         if (p.y > 0) {
             const int32_t c1 = __ldg(&sd.lvl_chunk[p.x + 1]);
-            for (int32_t c = __ldg(&sd.lvl_chunk[p.x]) + gw; c < c1; c += nw)
-                process_chunk<T, L, R, false>(sd, c, out, cx);
+            for (int32_t c = __ldg(&sd.lvl_chunk[p.x]) + gw; c < c1; c += nw) {
+                if (R == 1 && c == staged) finish_any<T, L, false>(sd, c, sg, out, cx);
+                else process_chunk<T, L, R, false>(sd, c, out, cx);
+            }
         } else if ((int)blockIdx.x == ph % (int)gridDim.x) {
             for (int32_t l = p.x; l < -p.y; ++l) {
                 const int32_t c1 = __ldg(&sd.lvl_chunk[l + 1]);
-                for (int32_t c = __ldg(&sd.lvl_chunk[l]) + wib; c < c1; c += wpb)
-                    process_chunk<T, L, R, false>(sd, c, out, cx);
+                for (int32_t c = __ldg(&sd.lvl_chunk[l]) + wib; c < c1; c += wpb) {
+                    if (R == 1 && c == staged) finish_any<T, L, false>(sd, c, sg, out, cx);
+                    else process_chunk<T, L, R, false>(sd, c, out, cx);
+                }
+                if (R == 1 && l + 1 < -p.y) {
+                    const int32_t c = __ldg(&sd.lvl_chunk[l + 1]) + wib;
+                    staged = c < __ldg(&sd.lvl_chunk[l + 2]) ? c : -1;
+                    if (staged >= 0) stage_chunk<T, L>(sd, staged, sg);
+                }
                 __syncthreads();
             }
+        }
+        if (R == 1) {
+            staged = first_chunk_of_phase<T>(sd, ph + 1, gw, wib);
+            if (staged >= 0) stage_chunk<T, L>(sd, staged, sg);
         }
         if (ph + 1 < sd.nphases && !grid_barrier(st, (++bar) * gridDim.x, timeout_ns, ph))
             break;
@@ -234,7 +362,7 @@ __global__ void __launch_bounds__(1024)
 solve_syncfree_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr,
                       DevStatus *st, uint64_t timeout_ns, int skip_if_converged) {
     if (skip_if_converged && converged(st)) return;
-    const Ctx cx{rhs, ld, nr, st, timeout_ns};
+    const Ctx cx{rhs, ld, nr, st, timeout_ns, sd.backoff_ns};
     const int wpb = blockDim.x >> 5;
     const int32_t gw = blockIdx.x * wpb + (threadIdx.x >> 5);
     const int32_t nw = gridDim.x * wpb;
@@ -242,8 +370,28 @@ solve_syncfree_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr
     // with every warp resident, the lowest unfinished chunk's warp has
     // finished its earlier chunks and all that chunk's dependencies lie in
     // earlier levels, so some warp can always make progress.
-    for (int32_t c = gw; c < sd.nchunks; c += nw)
-        if (process_chunk<T, L, R, true>(sd, c, out, cx)) break;
+    if (R > 1) {
+        for (int32_t c = gw; c < sd.nchunks; c += nw)
+            if (process_chunk<T, L, R, true>(sd, c, out, cx)) break;
+        return;
+    }
+    // One right-hand side: three-stage pipeline per warp -- meta of chunk
+    // c + 2 nw and entries of chunk c + nw are in flight while chunk c waits.
+    int32_t c = gw;
+    if (c >= sd.nchunks) return;
+    Staged<T> cur;
+    stage_chunk<T, L>(sd, c, cur);
+    int4 mt_next = c + nw < sd.nchunks ? __ldg(&sd.meta[c + nw]) : no_chunk();
+    while (c < sd.nchunks) {
+        Staged<T> nxt;
+        nxt.mt = mt_next;
+        stage_entries<T, L>(sd, nxt);
+        const int32_t c2 = c + 2 * nw;
+        mt_next = c2 < sd.nchunks ? __ldg(&sd.meta[c2]) : no_chunk();
+        if (finish_any<T, L, true>(sd, c, cur, out, cx)) break;
+        cur = nxt;
+        c += nw;
+    }
 }
 
 template <typename T>

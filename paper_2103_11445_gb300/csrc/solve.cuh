@@ -26,6 +26,7 @@ struct SolveData {
     const T *diag;              // solve position -> L_ii
     const int2 *phases;         // barrier schedule: (l0, l1) level, or (l0, -l1) CTA-local run
     int32_t nphases;
+    int32_t backoff_ns;         // sleep between failed polls (synchronisation-free), 0 = none
 };
 
 struct LaunchCfg {
