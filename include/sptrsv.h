@@ -106,7 +106,7 @@ typedef struct {
     int32_t ir_max_iter;     /* F32_IR: refinement steps at most (default 8,
                                 0 = plain FP32 solve, < 0 = default, max 64) */
     int32_t lanes_per_row;   /* 1,2,4,8,16,32; 0 = auto */
-    int32_t block_threads;   /* 128..1024, multiple of 32; 0 = auto */
+    int32_t block_threads;   /* 64..512, multiple of 32; 0 = auto */
     int32_t cta_run_rows;    /* levels of at most this many rows run inside
                                 one CTA (no grid barrier); 0 = auto, <0 = off */
     int32_t wait_timeout_ms; /* bound on every device wait (default 5000); a

@@ -316,7 +316,7 @@ sptrsv_status_t build_struct(sptrsv_plan_t p, SolveStruct<T> &ss, int L, cudaStr
     CK(ss.ecol.alloc(total));
     CK(ss.eval.alloc(total));
     CK(ss.row_id.alloc(p->n));
-    CK(ss.diag.alloc(p->n));
+    CK(ss.diag.alloc(2 * (size_t)p->n));
     CK(launch_chunk_fill<T>(nchunks, L, d_row0.p, d_nrows.p, d_width.p, d_off.p, p->perm.p,
                             p->row_ptr.p, p->col.p, p->val.p, pos_item, p->rw_off.p,
                             p->rw_col.p, p->rw_val.p, ss.meta.p, ss.ecol.p, ss.eval.p,
@@ -324,6 +324,7 @@ sptrsv_status_t build_struct(sptrsv_plan_t p, SolveStruct<T> &ss, int L, cudaStr
     CK(ss.chunk_level.alloc(nchunks));
     CK(launch_chunk_level(nseg, ss.lvl_chunk.p, ss.chunk_level.p, s));
     CK(cudaStreamSynchronize(s));
+    ss.n = p->n;
     ss.nlev = nseg;
     ss.nchunks = nchunks;
     ss.L = L;
@@ -498,9 +499,9 @@ sptrsv_status_t autotune(sptrsv_plan_t p, cudaStream_t s) {
     }
     // launch shape around the best layout and mode
     const SolveConfig base = best;
-    for (int bt : {256, 512, 1024}) {
+    for (int bt : {128, 256, 512}) {
         if (bt_req > 0 && bt != bt_req) continue;
-        for (int per_sm : {1, 2, 4}) {
+        for (int per_sm : {1, 2, 4, 8}) {
             SolveConfig c = base;
             c.block_threads = bt;
             c.grid = per_sm * p->num_sms;
@@ -790,7 +791,7 @@ sptrsv_status_t sptrsv_transform(sptrsv_plan_t p, const sptrsv_transform_params_
         prm->lanes_per_row != 32)
         return SPTRSV_ERR_INVALID_ARG;
     if (prm->block_threads != 0 &&
-        (prm->block_threads < 64 || prm->block_threads > 1024 || prm->block_threads % 32))
+        (prm->block_threads < 64 || prm->block_threads > 512 || prm->block_threads % 32))
         return SPTRSV_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const double t0 = now_ms();

@@ -7,7 +7,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/sptrsv.h"
+#include "sptrsv.h"
 
 namespace sptrsv {
 
@@ -129,6 +129,57 @@ __device__ __forceinline__ bool grid_barrier(DevStatus *st, unsigned long long t
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// Split form of grid_barrier: grid_arrive publishes this CTA's stores and
+// counts it in; the CTA may then issue loads of data that does not depend on
+// other CTAs (they stay in flight across the wait); grid_wait spins until
+// every CTA arrived.  Thread 0 does both, so the fence in grid_arrive never
+// has to wait for the loads issued in between.
+__device__ __forceinline__ void grid_arrive(DevStatus *st) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        red_release_add_u64(&st->bar_count, 1ull);
+    }
+}
+__device__ __forceinline__ bool grid_wait(DevStatus *st, unsigned long long target,
+                                          uint64_t timeout_ns, int where) {
+    __shared__ int s_ok2;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if (ld_acquire_u64(&st->bar_count) < target) {
+            WaitBudget wb(timeout_ns);
+            unsigned it = 0;
+            while (ld_acquire_u64(&st->bar_count) < target) {
+                if ((++it & kPollMask) == 0 && wb.expired(st, where)) { ok = 0; break; }
+            }
+        }
+        s_ok2 = ok;
+    }
+    __syncthreads();
+    return s_ok2 != 0;
+}
+
+// Bulk prefetch of [p, p + bytes) into L2 (TMA engine), shared out over the
+// grid: CTA b takes the b-th slice.  Only whole 16-byte units inside the
+// range are requested (the engine needs 16-byte aligned address and size).
+__device__ __forceinline__ void l2_prefetch_slice(const void *p, size_t bytes) {
+    if (threadIdx.x != 0 || p == nullptr || bytes == 0) return;
+    uintptr_t a = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+    const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+    if (e <= a) return;
+    const uintptr_t total = e - a;
+    uintptr_t slice = (total / gridDim.x + 15) & ~(uintptr_t)15;
+    if (slice < 4096) slice = 4096;
+    uintptr_t lo = a + slice * blockIdx.x;
+    if (lo >= e) return;
+    uintptr_t hi = lo + slice < e ? lo + slice : e;
+    constexpr uintptr_t kPiece = 1u << 16;
+    for (; lo < hi; lo += kPiece) {
+        const uint32_t sz = (uint32_t)(hi - lo < kPiece ? hi - lo : kPiece);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(lo), "r"(sz) : "memory");
+    }
 }
 
 // Called once by every CTA at the very end of a kernel that used

@@ -55,11 +55,12 @@ struct SolveStruct {
     DevArr<int4> meta;
     DevArr<T> eval, diag;
     DevArr<int2> phases;
-    int32_t nlev = 0, nchunks = 0, L = 1, nphases = 0;
+    int32_t n = 0, nlev = 0, nchunks = 0, L = 1, nphases = 0;
     int64_t nslots = 0;
     bool built = false;
     SolveData<T> view() const {
         SolveData<T> v;
+        v.n = n;
         v.nlev = nlev;
         v.nchunks = nchunks;
         v.L = L;

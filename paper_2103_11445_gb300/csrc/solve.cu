@@ -24,6 +24,11 @@ template <typename T> struct Bits;
 template <> struct Bits<double> {
     using U = unsigned long long;
     static __device__ __forceinline__ U load(const double *p) { return ld_relaxed_u64(p); }
+    static __device__ __forceinline__ U poll(const double *p) {
+        U v;
+        asm volatile("ld.volatile.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+        return v;
+    }
     static __device__ __forceinline__ void store(double *p, double v) {
         U b = (U)__double_as_longlong(v);
         if (b == Sentinel<double>::bits) b = 0x7FF8000000000000ull;
@@ -35,6 +40,11 @@ template <> struct Bits<double> {
 template <> struct Bits<float> {
     using U = unsigned;
     static __device__ __forceinline__ U load(const float *p) { return ld_relaxed_u32(p); }
+    static __device__ __forceinline__ U poll(const float *p) {
+        U v;
+        asm volatile("ld.volatile.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+        return v;
+    }
     static __device__ __forceinline__ void store(float *p, float v) {
         U b = __float_as_uint(v);
         if (b == Sentinel<float>::bits) b = 0x7FC00000u;
@@ -47,7 +57,7 @@ template <> struct Bits<float> {
 // Value of an unknown written by another warp of this launch.
 template <typename T, bool SF>
 __device__ __forceinline__ T load_x(const T *p) {
-    if (SF) return Bits<T>::from(Bits<T>::load(p));
+    if (SF) return Bits<T>::from(Bits<T>::poll(p));
     return __ldcg(p);
 }
 
@@ -61,7 +71,7 @@ __device__ __forceinline__ T wait_x_inl(const T *p, DevStatus *st, uint64_t time
     do {
         if (backoff_ns) __nanosleep(backoff_ns);
         if ((++it & kPollMask) == 0 && wb.expired(st, -2)) { bail = true; return T(0); }
-        b = Bits<T>::load(p);
+        b = Bits<T>::poll(p);
     } while (b == Sentinel<T>::bits);
     return Bits<T>::from(b);
 }
@@ -74,6 +84,49 @@ template <typename T, bool SF>
 __device__ __forceinline__ void store_x(T *p, T v) {
     if (SF) Bits<T>::store(p, v);
     else *p = v;
+}
+
+// Division by the diagonal without an FP64/FP32 divide on the common path.
+// With y = RN(1/d) precomputed (0 when d lies outside the safe range),
+// q = RN(s y) is within an ulp of s/d, the remainder r = s - d q is exact
+// (one FMA), and RN(q + r y) is the correctly rounded quotient (Markstein,
+// "Computation of elementary functions on the IBM RISC System/6000
+// processor", IBM J. Res. Dev. 1990).  The argument needs the remainder to be
+// representable, so the numerator must stay well above the subnormal range
+// (|s| in [slo, shi)) and the result away from underflow and overflow
+// (|q| in [qlo, qhi)); everything else takes an IEEE division.
+template <typename T> struct DivRange;
+template <> struct DivRange<double> {
+    static constexpr double slo = 0x1p-900, shi = 0x1p+900;
+    static constexpr double qlo = 0x1p-1000, qhi = 0x1p+1000;
+};
+template <> struct DivRange<float> {
+    static constexpr float slo = 0x1p-100f, shi = 0x1p+100f;
+    static constexpr float qlo = 0x1p-120f, qhi = 0x1p+120f;
+};
+
+template <typename T>
+__device__ __forceinline__ T div_by_diag(T s, T d, T y) {
+    const T as = fabs(s);
+    if (y != T(0) && as >= DivRange<T>::slo && as < DivRange<T>::shi) {
+        const T q = s * y;
+        const T r = fma(-q, d, s);
+        const T q2 = fma(r, y, q);
+        const T a = fabs(q2);
+        if (a >= DivRange<T>::qlo && a < DivRange<T>::qhi) return q2;
+    }
+    return s / d;
+}
+
+template <typename T> struct Vec2;
+template <> struct Vec2<double> { using V = double2; };
+template <> struct Vec2<float> { using V = float2; };
+
+template <typename T>
+__device__ __forceinline__ void load_diag(const SolveData<T> &sd, int32_t p, T &d, T &y) {
+    const typename Vec2<T>::V v = __ldg(reinterpret_cast<const typename Vec2<T>::V *>(sd.diag) + p);
+    d = v.x;
+    y = v.y;
 }
 
 struct Ctx {
@@ -95,6 +148,13 @@ __device__ __forceinline__ bool chunk_one(const SolveData<T> &sd, int32_t c, T *
     const bool active = k < mt.y;
     T acc = T(0);
     bool bail = false;
+    int32_t r = 0;
+    T brow = T(0), dg = T(1), dy = T(1);
+    if (active && s == 0) {  // independent of every unknown: issue first
+        r = __ldg(&sd.row_id[mt.x + k]);
+        load_diag<T>(sd, mt.x + k, dg, dy);
+        brow = (T)__ldg(cx.rhs + (int64_t)r * cx.ld);
+    }
     if (active) {
         const int64_t stride = (int64_t)mt.y * L;
         const int32_t *cp = sd.ecol + mt.w + k * L + s;
@@ -115,12 +175,15 @@ __device__ __forceinline__ bool chunk_one(const SolveData<T> &sd, int32_t c, T *
                 else if (cc[u] != PAD_COL) xv[u] = (T)__ldg(cx.rhs + (int64_t)(~cc[u]) * cx.ld);
                 else xv[u] = T(0);
             }
+            T pr[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (SF && cc[u] >= 0 && Bits<T>::of(xv[u]) == Sentinel<T>::bits)
                     xv[u] = wait_x<T>(out + (int64_t)cc[u] * cx.ld, cx.st, cx.timeout_ns, bail);
-                acc = fma(vv[u], xv[u], acc);
+                pr[u] = vv[u] * xv[u];
             }
+            // fixed-order tree: few dependent FP64 operations after the last arrival
+            acc += (pr[0] + pr[1]) + (pr[2] + pr[3]);
         }
         for (; step < mt.z; ++step) {
             const int32_t cc = __ldg(cp + (int64_t)step * stride);
@@ -138,12 +201,7 @@ __device__ __forceinline__ bool chunk_one(const SolveData<T> &sd, int32_t c, T *
     }
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
-    if (active && s == 0) {
-        const int32_t p = mt.x + k;
-        const int32_t r = __ldg(&sd.row_id[p]);
-        const T res = ((T)__ldg(cx.rhs + (int64_t)r * cx.ld) - acc) / __ldg(&sd.diag[p]);
-        store_x<T, SF>(out + (int64_t)r * cx.ld, res);
-    }
+    if (active && s == 0) store_x<T, SF>(out + (int64_t)r * cx.ld, div_by_diag<T>(brow - acc, dg, dy));
     return __any_sync(FULL_MASK, bail);
 }
 
@@ -163,6 +221,13 @@ __device__ __forceinline__ bool chunk_multi(const SolveData<T> &sd, int32_t c, T
         const bool rowok = k < mt.y;
         const bool active = rowok && r < cx.nr;
         T acc = T(0);
+        int32_t row = 0;
+        T brow = T(0), dg = T(1), dy = T(1);
+        if (active) {  // independent of every unknown: issue first
+            row = __ldg(&sd.row_id[mt.x + k]);
+            load_diag<T>(sd, mt.x + k, dg, dy);
+            brow = (T)__ldg(cx.rhs + (int64_t)row * cx.ld + r);
+        }
         if (rowok) {
             const int64_t base = mt.w + (int64_t)k * L;
             for (int step = 0; step < mt.z; ++step) {
@@ -184,12 +249,8 @@ __device__ __forceinline__ bool chunk_multi(const SolveData<T> &sd, int32_t c, T
                 }
             }
         }
-        if (active) {
-            const int32_t p = mt.x + k;
-            const int32_t row = __ldg(&sd.row_id[p]);
-            const T res = ((T)__ldg(cx.rhs + (int64_t)row * cx.ld + r) - acc) / __ldg(&sd.diag[p]);
-            store_x<T, SF>(out + (int64_t)row * cx.ld + r, res);
-        }
+        if (active)
+            store_x<T, SF>(out + (int64_t)row * cx.ld + r, div_by_diag<T>(brow - acc, dg, dy));
         if (__any_sync(FULL_MASK, bail)) return true;
     }
     return false;
@@ -203,12 +264,17 @@ __device__ __forceinline__ bool chunk_multi(const SolveData<T> &sd, int32_t c, T
 // wait for its dependencies remain.  Chunks wider than kPipeSteps entries
 // per lane go through chunk_one.
 constexpr int kPipeSteps = 4;
+// Largest CTA of the solve kernels: 512 threads leave 128 registers per
+// thread, enough for the staged chunk without spilling.
+constexpr int kMaxSolveThreads = 512;
 
 template <typename T>
 struct Staged {
     int4 mt;
     int32_t col[kPipeSteps];
     T val[kPipeSteps];
+    int32_t row;   // row of this lane's chunk row (lane s == 0 only)
+    T diag, rdiag;
 };
 
 __device__ __forceinline__ int4 no_chunk() { return make_int4(0, 0, 0, 0); }
@@ -230,6 +296,15 @@ __device__ __forceinline__ void stage_entries(const SolveData<T> &sd, Staged<T> 
             sg.val[u] = T(0);
         }
     }
+    // the row and its diagonal do not depend on any unknown: load them now
+    if (k < sg.mt.y && s == 0) {
+        sg.row = __ldg(&sd.row_id[sg.mt.x + k]);
+        load_diag<T>(sd, sg.mt.x + k, sg.diag, sg.rdiag);
+    } else {
+        sg.row = 0;
+        sg.diag = T(1);
+        sg.rdiag = T(1);
+    }
 }
 
 template <typename T, int L, bool SF>
@@ -238,6 +313,8 @@ __device__ __forceinline__ bool finish_staged(const SolveData<T> &sd, const Stag
     const int lane = threadIdx.x & 31;
     const int k = lane / L, s = lane % L;
     const bool active = k < sg.mt.y;
+    // b_i first: nothing after the wait may be another dependent load
+    const T brow = (active && s == 0) ? (T)__ldg(cx.rhs + (int64_t)sg.row * cx.ld) : T(0);
     T xv[kPipeSteps];
 #pragma unroll
     for (int u = 0; u < kPipeSteps; ++u) {
@@ -247,22 +324,20 @@ __device__ __forceinline__ bool finish_staged(const SolveData<T> &sd, const Stag
         else xv[u] = T(0);
     }
     bool bail = false;
-    T acc = T(0);
+    T pr[kPipeSteps];
 #pragma unroll
     for (int u = 0; u < kPipeSteps; ++u) {
         if (SF && sg.col[u] >= 0 && Bits<T>::of(xv[u]) == Sentinel<T>::bits)
             xv[u] = wait_x_inl<T>(out + (int64_t)sg.col[u] * cx.ld, cx.st, cx.timeout_ns,
                                   cx.backoff_ns, bail);
-        acc = fma(sg.val[u], xv[u], acc);
+        pr[u] = sg.val[u] * xv[u];
     }
+    // short dependency chain after the last arrival (FP64 latency is long)
+    T acc = (pr[0] + pr[1]) + (pr[2] + pr[3]);
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
-    if (active && s == 0) {
-        const int32_t p = sg.mt.x + k;
-        const int32_t r = __ldg(&sd.row_id[p]);
-        const T res = ((T)__ldg(cx.rhs + (int64_t)r * cx.ld) - acc) / __ldg(&sd.diag[p]);
-        store_x<T, SF>(out + (int64_t)r * cx.ld, res);
-    }
+    if (active && s == 0)
+        store_x<T, SF>(out + (int64_t)sg.row * cx.ld, div_by_diag<T>(brow - acc, sg.diag, sg.rdiag));
     return __any_sync(FULL_MASK, bail);
 }
 
@@ -290,6 +365,23 @@ __device__ __forceinline__ bool converged(const DevStatus *st) {
     return ld_relaxed_u64(&st->ir_flag) != 0ull;
 }
 
+// Start of every solve kernel: pull the arrays that are read by row (meta,
+// row_id, diag) and the right-hand side into L2, so that gathers from them
+// hit L2 instead of HBM.  The rhs prefetch is capped at 64 MiB.
+template <typename T>
+__device__ __forceinline__ void prefetch_solve_inputs(const SolveData<T> &sd, const double *rhs,
+                                                      int64_t n, int ld, int nr) {
+    l2_prefetch_slice(sd.meta, (size_t)sd.nchunks * sizeof(int4));
+    l2_prefetch_slice(sd.row_id, (size_t)n * sizeof(int32_t));
+    l2_prefetch_slice(sd.diag, (size_t)n * 2 * sizeof(T));
+    // rhs points at column c0 of a row-major [n, ld] array: the last element
+    // this launch reads is ((n - 1) * ld + nr - 1), so stay inside that
+    if (n <= 0) return;
+    size_t rb = ((size_t)(n - 1) * ld + nr) * sizeof(double);
+    if (rb > (64u << 20)) rb = 64u << 20;
+    l2_prefetch_slice(rhs, rb);
+}
+
 // The warp's first chunk of phase ph (or -1): fat levels are shared by the
 // whole grid, a CTA-local run belongs to CTA ph % gridDim.x.
 template <typename T>
@@ -307,7 +399,7 @@ __device__ __forceinline__ int32_t first_chunk_of_phase(const SolveData<T> &sd, 
 }
 
 template <typename T, int L, int R>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(kMaxSolveThreads)
 solve_barrier_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr,
                      DevStatus *st, uint64_t timeout_ns, int skip_if_converged) {
     if (skip_if_converged && converged(st)) return;  // uniform: set by an earlier kernel
@@ -316,6 +408,7 @@ solve_barrier_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr,
     const int32_t gw = blockIdx.x * wpb + wib;
     const int32_t nw = gridDim.x * wpb;
     unsigned long long bar = 0;
+    prefetch_solve_inputs<T>(sd, rhs, sd.n, ld, nr);
     // One right-hand side: the warp's first chunk of the next phase (or of
     // the next level of a run) is staged before the barrier that precedes it.
     Staged<T> sg;
@@ -347,18 +440,18 @@ solve_barrier_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr,
                 __syncthreads();
             }
         }
+        if (ph + 1 < sd.nphases) grid_arrive(st);
         if (R == 1) {
             staged = first_chunk_of_phase<T>(sd, ph + 1, gw, wib);
             if (staged >= 0) stage_chunk<T, L>(sd, staged, sg);
         }
-        if (ph + 1 < sd.nphases && !grid_barrier(st, (++bar) * gridDim.x, timeout_ns, ph))
-            break;
+        if (ph + 1 < sd.nphases && !grid_wait(st, (++bar) * gridDim.x, timeout_ns, ph)) break;
     }
     grid_exit(st);
 }
 
 template <typename T, int L, int R>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(kMaxSolveThreads)
 solve_syncfree_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr,
                       DevStatus *st, uint64_t timeout_ns, int skip_if_converged) {
     if (skip_if_converged && converged(st)) return;
@@ -366,32 +459,16 @@ solve_syncfree_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr
     const int wpb = blockDim.x >> 5;
     const int32_t gw = blockIdx.x * wpb + (threadIdx.x >> 5);
     const int32_t nw = gridDim.x * wpb;
+    prefetch_solve_inputs<T>(sd, rhs, sd.n, ld, nr);
     // Chunks are taken in level order, each warp its own arithmetic sequence:
     // with every warp resident, the lowest unfinished chunk's warp has
     // finished its earlier chunks and all that chunk's dependencies lie in
     // earlier levels, so some warp can always make progress.
-    if (R > 1) {
-        for (int32_t c = gw; c < sd.nchunks; c += nw)
-            if (process_chunk<T, L, R, true>(sd, c, out, cx)) break;
-        return;
-    }
-    // One right-hand side: three-stage pipeline per warp -- meta of chunk
-    // c + 2 nw and entries of chunk c + nw are in flight while chunk c waits.
-    int32_t c = gw;
-    if (c >= sd.nchunks) return;
-    Staged<T> cur;
-    stage_chunk<T, L>(sd, c, cur);
-    int4 mt_next = c + nw < sd.nchunks ? __ldg(&sd.meta[c + nw]) : no_chunk();
-    while (c < sd.nchunks) {
-        Staged<T> nxt;
-        nxt.mt = mt_next;
-        stage_entries<T, L>(sd, nxt);
-        const int32_t c2 = c + 2 * nw;
-        mt_next = c2 < sd.nchunks ? __ldg(&sd.meta[c2]) : no_chunk();
-        if (finish_any<T, L, true>(sd, c, cur, out, cx)) break;
-        cur = nxt;
-        c += nw;
-    }
+    // (Staging the next chunk's entries while this one waits measured slower
+    // here than processing each chunk in turn: the staged loads compete with
+    // the polls and pin registers; the barrier kernel keeps its staging.)
+    for (int32_t c = gw; c < sd.nchunks; c += nw)
+        if (process_chunk<T, L, R, true>(sd, c, out, cx)) break;
 }
 
 template <typename T>

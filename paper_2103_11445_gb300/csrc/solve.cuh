@@ -15,6 +15,7 @@ namespace sptrsv {
 // is an x term, ecol < 0 (not PAD_COL) a b term of a rewritten row.
 template <typename T>
 struct SolveData {
+    int32_t n;                  // rows
     int32_t nlev;
     int32_t nchunks;
     int32_t L;                  // lanes per row of the layout
@@ -23,7 +24,7 @@ struct SolveData {
     const int32_t *ecol;
     const T *eval;
     const int32_t *row_id;      // solve position -> row
-    const T *diag;              // solve position -> L_ii
+    const T *diag;              // solve position p -> (L_ii, RN(1/L_ii) or 0) at [2p], [2p+1]
     const int2 *phases;         // barrier schedule: (l0, l1) level, or (l0, -l1) CTA-local run
     int32_t nphases;
     int32_t backoff_ns;         // sleep between failed polls (synchronisation-free), 0 = none

@@ -323,7 +323,13 @@ __global__ void chunk_fill_kernel(int32_t nchunks, int H, int L,
     const int32_t r = perm[p];
     row_id[p] = r;
     const int32_t dpos = row_ptr[r + 1] - 1;
-    diag[p] = (T)val[dpos];
+    // (L_ii, RN(1/L_ii)); the reciprocal is 0 where the solve must divide
+    const T d = (T)val[dpos];
+    const T ad = fabs(d);
+    const bool safe = sizeof(T) == 8 ? (ad >= (T)0x1p-1000 && ad <= (T)0x1p+1000)
+                                     : (ad >= (T)0x1p-120f && ad <= (T)0x1p+120f);
+    diag[2 * (int64_t)p] = d;
+    diag[2 * (int64_t)p + 1] = safe ? T(1) / d : T(0);
     const int32_t it = pos_item ? pos_item[p] : -1;
     const int64_t stride = (int64_t)nr * L;
     int32_t len;

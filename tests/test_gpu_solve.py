@@ -59,6 +59,25 @@ def test_closed_forms(mode):
 
 
 @pytest.mark.parametrize("mode", B_MODES, ids=["barrier", "barrier_runs", "syncfree"])
+def test_diagonal_division_is_correctly_rounded(mode):
+    """x_i = b_i / d_i must be the IEEE quotient bit for bit over the whole
+    exponent range, zeros, subnormals, infinities and NaN included."""
+    rng = np.random.default_rng(11)
+    n = 200_000
+    d = rng.choice([-1.0, 1.0], n) * np.exp2(rng.uniform(-1060, 1060, n))
+    b = rng.choice([-1.0, 1.0], n) * np.exp2(rng.uniform(-1074, 1023, n))
+    d[:8] = [1.0, -3.0, 5e-324, 2.0 ** -1000, 2.0 ** 1000, 1.7e308, -4.9e-324, 0.1]
+    b[:8] = [0.0, -0.0, 1.0, np.inf, -np.inf, np.nan, 3.0, 5e-324]
+    d = np.where(d == 0.0, 1.0, d)
+    A = mg.CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), d)
+    with np.errstate(all="ignore"):
+        ref = b / d
+    x = gpu_solve(plan_for(A, **plain(**mode)), b)
+    same = (x.view(np.uint64) == ref.view(np.uint64)) | (np.isnan(x) & np.isnan(ref))
+    assert same.all(), np.nonzero(~same)[0][:10]
+
+
+@pytest.mark.parametrize("mode", B_MODES, ids=["barrier", "barrier_runs", "syncfree"])
 def test_random_small_matrices(mode):
     for seed in range(4):
         A = mg.random_lower(257, seed=seed, density=0.08)
