@@ -198,6 +198,40 @@ SPTRSV_API sptrsv_status_t sptrsv_get_transformed(sptrsv_plan_t p, int32_t *d_ne
                                        int32_t *d_bcol, double *d_bw,
                                        sptrsv_stream_t stream);
 
+/* Batched solve (the paper treats one matrix; this serves many independent
+ * systems of uneven size at once).  All plans must live on the current
+ * device, be transformed with the same precision, and stay alive (and not be
+ * transformed again) while the batch exists; at most as many plans as the
+ * GPU holds co-resident CTAs (SPTRSV_ERR_UNSUPPORTED otherwise).  Refinement
+ * tolerance, step limit (<= 16) and wait bound come from the first plan. */
+SPTRSV_API sptrsv_status_t sptrsv_batch_create(const sptrsv_plan_t *plans, int32_t count,
+                                               sptrsv_batch_t *out);
+
+/* Solves every plan's system in ONE persistent launch: matrix i owns a group
+ * of CTAs sized by its bytes, solves synchronisation-free inside the group
+ * and separates the refinement phases (FP32 solve, FP64 residual, FP32
+ * correction) with barriers on its own counter.  h_b / h_x are host arrays
+ * of `count` device pointers to row-major [n_i, h_nrhs[i]] buffers
+ * (1 <= h_nrhs[i] <= 32).  On a non-default stream the sequence is captured
+ * in a CUDA graph on the first call and replayed afterwards (re-captured if
+ * the scratch must grow); the first call, which may allocate, should come
+ * before any stream capture of the caller's own.  Waits for the previous
+ * batch_solve on this batch to finish before reusing its staging table. */
+SPTRSV_API sptrsv_status_t sptrsv_batch_solve(sptrsv_batch_t batch, const double *const *h_b,
+                                              double *const *h_x, const int32_t *h_nrhs,
+                                              sptrsv_stream_t stream);
+
+/* Synchronise `stream` and return an error a batch kernel latched. */
+SPTRSV_API sptrsv_status_t sptrsv_batch_check(sptrsv_batch_t batch, sptrsv_stream_t stream);
+
+/* After the last batch_solve completed: per matrix the refinement steps
+ * applied, whether the tolerance was met, and the CTAs of its group; whether
+ * the launch ran from a CUDA graph.  Any pointer may be NULL. */
+SPTRSV_API sptrsv_status_t sptrsv_batch_get_info(sptrsv_batch_t batch, int32_t *h_iters,
+                                                 int32_t *h_converged, int32_t *h_cta_count,
+                                                 int32_t *h_graph);
+SPTRSV_API void sptrsv_batch_destroy(sptrsv_batch_t batch);
+
 /* The FP32 + FP64-refinement solve without any device allocation.  The
  * paper has no counterpart: this exists for callers that cannot call
  * cudaMalloc when they solve -- code recording a CUDA graph, applications

@@ -85,6 +85,11 @@ _SIGS = {
                                          c_void_p, c_void_p, c_void_p, c_void_p,
                                          c_void_p]),
     "sptrsv_debug_inject_wait": (c_int32, [c_void_p, c_int32]),
+    "sptrsv_batch_create": (c_int32, [c_void_p, c_int32, POINTER(c_void_p)]),
+    "sptrsv_batch_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sptrsv_batch_check": (c_int32, [c_void_p, c_void_p]),
+    "sptrsv_batch_get_info": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sptrsv_batch_destroy": (None, [c_void_p]),
     "sptrsv_set_profiling": (c_int32, [c_void_p, c_int32]),
     "sptrsv_solve_ir_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "sptrsv_last_kernel_ms": (c_int32, [c_void_p, POINTER(ctypes.c_float)]),
@@ -207,6 +212,39 @@ def sptrsv_last_kernel_ms(plan: int) -> float:
     ms = ctypes.c_float()
     _check(load().sptrsv_last_kernel_ms(plan, byref(ms)), "sptrsv_last_kernel_ms")
     return float(ms.value)
+
+
+def sptrsv_batch_create(plans) -> int:
+    arr = (c_void_p * len(plans))(*plans)
+    out = c_void_p()
+    _check(load().sptrsv_batch_create(arr, len(plans), byref(out)), "sptrsv_batch_create")
+    return out.value
+
+
+def sptrsv_batch_solve(batch: int, b_ptrs, x_ptrs, nrhs, stream: int = 0) -> None:
+    m = len(b_ptrs)
+    bp = (c_void_p * m)(*b_ptrs)
+    xp = (c_void_p * m)(*x_ptrs)
+    nr = (c_int32 * m)(*nrhs)
+    _check(load().sptrsv_batch_solve(batch, bp, xp, nr, stream), "sptrsv_batch_solve")
+
+
+def sptrsv_batch_check(batch: int, stream: int = 0) -> int:
+    return int(load().sptrsv_batch_check(batch, stream))
+
+
+def sptrsv_batch_get_info(batch: int, count: int):
+    it = (c_int32 * count)()
+    cv = (c_int32 * count)()
+    ct = (c_int32 * count)()
+    g = c_int32()
+    _check(load().sptrsv_batch_get_info(batch, it, cv, ct, byref(g)), "sptrsv_batch_get_info")
+    return dict(iters=list(it), converged=list(cv), cta_count=list(ct), graph=g.value)
+
+
+def sptrsv_batch_destroy(batch: int) -> None:
+    if batch:
+        load().sptrsv_batch_destroy(batch)
 
 
 # --- torch convenience wrapper ---------------------------------------------

@@ -136,7 +136,12 @@ struct Ctx {
     DevStatus *st;
     uint64_t timeout_ns;
     int backoff_ns;
+    bool rhs_coherent;   // rhs was written earlier in this launch: read it through L2
 };
+
+__device__ __forceinline__ double load_rhs(const Ctx &cx, int64_t i) {
+    return cx.rhs_coherent ? __ldcg(cx.rhs + i) : __ldg(cx.rhs + i);
+}
 
 // One right-hand side; L lanes per row (compile time).
 template <typename T, int L, bool SF>
@@ -153,7 +158,7 @@ __device__ __forceinline__ bool chunk_one(const SolveData<T> &sd, int32_t c, T *
     if (active && s == 0) {  // independent of every unknown: issue first
         r = __ldg(&sd.row_id[mt.x + k]);
         load_diag<T>(sd, mt.x + k, dg, dy);
-        brow = (T)__ldg(cx.rhs + (int64_t)r * cx.ld);
+        brow = (T)load_rhs(cx, (int64_t)r * cx.ld);
     }
     if (active) {
         const int64_t stride = (int64_t)mt.y * L;
@@ -172,7 +177,7 @@ __device__ __forceinline__ bool chunk_one(const SolveData<T> &sd, int32_t c, T *
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (cc[u] >= 0) xv[u] = load_x<T, SF>(out + (int64_t)cc[u] * cx.ld);
-                else if (cc[u] != PAD_COL) xv[u] = (T)__ldg(cx.rhs + (int64_t)(~cc[u]) * cx.ld);
+                else if (cc[u] != PAD_COL) xv[u] = (T)load_rhs(cx, (int64_t)(~cc[u]) * cx.ld);
                 else xv[u] = T(0);
             }
             T pr[U];
@@ -194,7 +199,7 @@ __device__ __forceinline__ bool chunk_one(const SolveData<T> &sd, int32_t c, T *
                 if (SF && Bits<T>::of(xv) == Sentinel<T>::bits)
                     xv = wait_x<T>(out + (int64_t)cc * cx.ld, cx.st, cx.timeout_ns, bail);
             } else if (cc != PAD_COL) {
-                xv = (T)__ldg(cx.rhs + (int64_t)(~cc) * cx.ld);
+                xv = (T)load_rhs(cx, (int64_t)(~cc) * cx.ld);
             }
             acc = fma(v, xv, acc);
         }
@@ -226,7 +231,7 @@ __device__ __forceinline__ bool chunk_multi(const SolveData<T> &sd, int32_t c, T
         if (active) {  // independent of every unknown: issue first
             row = __ldg(&sd.row_id[mt.x + k]);
             load_diag<T>(sd, mt.x + k, dg, dy);
-            brow = (T)__ldg(cx.rhs + (int64_t)row * cx.ld + r);
+            brow = (T)load_rhs(cx, (int64_t)row * cx.ld + r);
         }
         if (rowok) {
             const int64_t base = mt.w + (int64_t)k * L;
@@ -243,7 +248,7 @@ __device__ __forceinline__ bool chunk_multi(const SolveData<T> &sd, int32_t c, T
                         if (SF && Bits<T>::of(xv) == Sentinel<T>::bits)
                             xv = wait_x<T>(px, cx.st, cx.timeout_ns, bail);
                     } else {
-                        xv = (T)__ldg(cx.rhs + (int64_t)(~cc) * cx.ld + r);
+                        xv = (T)load_rhs(cx, (int64_t)(~cc) * cx.ld + r);
                     }
                     acc = fma(v, xv, acc);
                 }
@@ -276,8 +281,6 @@ struct Staged {
     int32_t row;   // row of this lane's chunk row (lane s == 0 only)
     T diag, rdiag;
 };
-
-__device__ __forceinline__ int4 no_chunk() { return make_int4(0, 0, 0, 0); }
 
 template <typename T, int L>
 __device__ __forceinline__ void stage_entries(const SolveData<T> &sd, Staged<T> &sg) {
@@ -314,13 +317,13 @@ __device__ __forceinline__ bool finish_staged(const SolveData<T> &sd, const Stag
     const int k = lane / L, s = lane % L;
     const bool active = k < sg.mt.y;
     // b_i first: nothing after the wait may be another dependent load
-    const T brow = (active && s == 0) ? (T)__ldg(cx.rhs + (int64_t)sg.row * cx.ld) : T(0);
+    const T brow = (active && s == 0) ? (T)load_rhs(cx, (int64_t)sg.row * cx.ld) : T(0);
     T xv[kPipeSteps];
 #pragma unroll
     for (int u = 0; u < kPipeSteps; ++u) {
         const int32_t c = sg.col[u];
         if (c >= 0) xv[u] = load_x<T, SF>(out + (int64_t)c * cx.ld);
-        else if (c != PAD_COL) xv[u] = (T)__ldg(cx.rhs + (int64_t)(~c) * cx.ld);
+        else if (c != PAD_COL) xv[u] = (T)load_rhs(cx, (int64_t)(~c) * cx.ld);
         else xv[u] = T(0);
     }
     bool bail = false;
@@ -403,7 +406,7 @@ __global__ void __launch_bounds__(kMaxSolveThreads)
 solve_barrier_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr,
                      DevStatus *st, uint64_t timeout_ns, int skip_if_converged) {
     if (skip_if_converged && converged(st)) return;  // uniform: set by an earlier kernel
-    const Ctx cx{rhs, ld, nr, st, timeout_ns, 0};
+    const Ctx cx{rhs, ld, nr, st, timeout_ns, 0, false};
     const int wpb = blockDim.x >> 5, wib = threadIdx.x >> 5;
     const int32_t gw = blockIdx.x * wpb + wib;
     const int32_t nw = gridDim.x * wpb;
@@ -455,7 +458,7 @@ __global__ void __launch_bounds__(kMaxSolveThreads)
 solve_syncfree_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr,
                       DevStatus *st, uint64_t timeout_ns, int skip_if_converged) {
     if (skip_if_converged && converged(st)) return;
-    const Ctx cx{rhs, ld, nr, st, timeout_ns, sd.backoff_ns};
+    const Ctx cx{rhs, ld, nr, st, timeout_ns, sd.backoff_ns, false};
     const int wpb = blockDim.x >> 5;
     const int32_t gw = blockIdx.x * wpb + (threadIdx.x >> 5);
     const int32_t nw = gridDim.x * wpb;
@@ -581,7 +584,175 @@ __global__ void ir_update_kernel(double *__restrict__ x, const float *__restrict
     x[i] = first ? (double)d[i] : x[i] + (double)d[i];
 }
 
+
+// ---------------------------------------------------------------------------
+// Batched persistent solve.
+
+__device__ __forceinline__ bool group_barrier(unsigned long long *cnt, unsigned long long target,
+                                              DevStatus *st, uint64_t timeout_ns) {
+    __shared__ int s_gok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        red_release_add_u64(cnt, 1ull);
+        if (ld_acquire_u64(cnt) < target) {
+            WaitBudget wb(timeout_ns);
+            unsigned it = 0;
+            while (ld_acquire_u64(cnt) < target) {
+                if ((++it & kPollMask) == 0 && wb.expired(st, -3)) { ok = 0; break; }
+            }
+        }
+        s_gok = ok;
+    }
+    __syncthreads();
+    return s_gok != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ bool batch_chunk(const SolveData<T> &sd, int32_t c, T *out,
+                                            const Ctx &cx, int R) {
+    switch (R) {
+    case 1: return chunk_multi<T, 1, true>(sd, c, out, cx);
+    case 2: return chunk_multi<T, 2, true>(sd, c, out, cx);
+    case 4: return chunk_multi<T, 4, true>(sd, c, out, cx);
+    case 8: return chunk_multi<T, 8, true>(sd, c, out, cx);
+    case 16: return chunk_multi<T, 16, true>(sd, c, out, cx);
+    default: return chunk_multi<T, 32, true>(sd, c, out, cx);
+    }
+}
+
+// sync-free solve of one matrix by the warps of its group; false on abort
+template <typename T>
+__device__ __forceinline__ bool batch_solve_group(const SolveData<T> &sd, const double *rhs,
+                                                  bool rhs_coherent, T *out, int nr, int R,
+                                                  DevStatus *st, uint64_t timeout_ns, int32_t gw,
+                                                  int32_t nw) {
+    const Ctx cx{rhs, nr, nr, st, timeout_ns, 0, rhs_coherent};
+    for (int32_t c = gw; c < sd.nchunks; c += nw)
+        if (batch_chunk<T>(sd, c, out, cx, R)) return false;
+    return true;
+}
+
+__device__ __forceinline__ void atomic_max_abs(unsigned long long *slot, double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL_MASK, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(slot, (unsigned long long)__double_as_longlong(v));
+}
+
+template <bool IR>
+__global__ void __launch_bounds__(kMaxSolveThreads)
+batch_kernel(const BatchMat *__restrict__ mats, int32_t nmats, BatchCtl *ctl, DevStatus *st,
+             double tol, int max_iter, uint64_t timeout_ns) {
+    __shared__ int32_t s_m;
+    if (threadIdx.x == 0) {
+        int32_t lo = 0, hi = nmats - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (mats[mid].cta_begin <= (int32_t)blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        s_m = lo;
+    }
+    __syncthreads();
+    const BatchMat &M = mats[s_m];
+    const int32_t j = (int32_t)blockIdx.x - M.cta_begin;
+    const int32_t G = M.cta_count;
+    if (j < 0 || j >= G || M.n == 0) return;
+    BatchCtl *C = ctl + s_m;
+    const int wpb = blockDim.x >> 5;
+    const int32_t gw = j * wpb + (threadIdx.x >> 5), nw = G * wpb;
+    const int64_t gt = (int64_t)j * blockDim.x + threadIdx.x, gthreads = (int64_t)G * blockDim.x;
+    const int64_t count = (int64_t)M.n * M.nr;
+    unsigned long long bar = 0;
+#define SPTRSV_GSYNC()                                                               \
+    if (!group_barrier(&C->bar, (++bar) * (unsigned long long)G, st, timeout_ns)) return
+    if (!IR) {
+        for (int64_t i = gt; i < count; i += gthreads)
+            *reinterpret_cast<unsigned long long *>(M.x + i) = Sentinel<double>::bits;
+        SPTRSV_GSYNC();
+        batch_solve_group<double>(M.s64, M.b, false, M.x, M.nr, M.R, st, timeout_ns, gw, nw);
+        return;
+    }
+    // FP32 solve, then FP64 residual / FP32 correction rounds
+    double bmax = 0.0;
+    for (int64_t i = gt; i < count; i += gthreads) {
+        *reinterpret_cast<unsigned *>(M.d32 + i) = Sentinel<float>::bits;
+        bmax = fmax(bmax, fabs(M.b[i]));
+    }
+    atomic_max_abs(&C->norms[0][2], bmax);
+    SPTRSV_GSYNC();
+    if (!batch_solve_group<float>(M.s32, M.b, false, M.d32, M.nr, M.R, st, timeout_ns, gw, nw)) return;
+    SPTRSV_GSYNC();
+    // values written by other CTAs of the group are read through L2 (__ldcg):
+    // this SM's L1 may hold stale copies of those lines
+    for (int64_t i = gt; i < count; i += gthreads) M.x[i] = (double)__ldcg(M.d32 + i);
+    int it = 0;
+    for (; it < max_iter; ++it) {
+        SPTRSV_GSYNC();
+        // r = b - L x and the infinity norms of r and x
+        double rmax = 0.0, xmax = 0.0;
+        for (int64_t row = gt; row < (int64_t)M.n; row += gthreads) {
+            const int32_t a = M.row_ptr[row], e = M.row_ptr[row + 1];
+            for (int c = 0; c < M.nr; ++c) {
+                double s = M.b[row * M.nr + c];
+                for (int32_t k = a; k < e; ++k)
+                    s -= M.val[k] * __ldcg(M.x + (int64_t)M.col[k] * M.nr + c);
+                M.r64[row * M.nr + c] = s;
+                rmax = fmax(rmax, fabs(s));
+                xmax = fmax(xmax, fabs(__ldcg(M.x + row * M.nr + c)));
+            }
+        }
+        atomic_max_abs(&C->norms[it][0], rmax);
+        atomic_max_abs(&C->norms[it][1], xmax);
+        SPTRSV_GSYNC();
+        const double rn = __longlong_as_double((long long)ld_relaxed_u64(&C->norms[it][0]));
+        const double xn = __longlong_as_double((long long)ld_relaxed_u64(&C->norms[it][1]));
+        const double bnorm = __longlong_as_double((long long)ld_relaxed_u64(&C->norms[0][2]));
+        if (rn <= tol * (M.lnorm * xn + bnorm)) break;
+        for (int64_t i = gt; i < count; i += gthreads)
+            *reinterpret_cast<unsigned *>(M.d32 + i) = Sentinel<float>::bits;
+        SPTRSV_GSYNC();
+        if (!batch_solve_group<float>(M.s32, M.r64, true, M.d32, M.nr, M.R, st, timeout_ns, gw, nw))
+            return;
+        SPTRSV_GSYNC();
+        for (int64_t i = gt; i < count; i += gthreads)
+            M.x[i] = __ldcg(M.x + i) + (double)__ldcg(M.d32 + i);
+    }
+    if (gt == 0) {
+        C->iters = it;
+        C->converged = it < max_iter ? 1 : 0;
+    }
+#undef SPTRSV_GSYNC
+}
 }  // namespace
+
+int batch_max_coresident(bool ir, int block_threads, int num_sms) {
+    int per_sm = 0;
+    const void *k = ir ? (const void *)batch_kernel<true> : (const void *)batch_kernel<false>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block_threads, 0) != cudaSuccess)
+        return 0;
+    return per_sm * num_sms;
+}
+
+cudaError_t launch_batch(const BatchMat *mats, int32_t nmats, BatchCtl *ctl, DevStatus *st,
+                         bool ir, double tol, int max_iter, uint64_t timeout_ns, int block_threads,
+                         int grid, cudaStream_t s) {
+    if (nmats == 0 || grid == 0) return cudaSuccess;
+    if (max_iter > kBatchMaxIter) max_iter = kBatchMaxIter;
+    void *args[] = {(void *)&mats, (void *)&nmats, (void *)&ctl, (void *)&st,
+                    (void *)&tol, (void *)&max_iter, (void *)&timeout_ns};
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(grid);
+    lc.blockDim = dim3(block_threads);
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    const void *k = ir ? (const void *)batch_kernel<true> : (const void *)batch_kernel<false>;
+    return cudaLaunchKernelExC(&lc, k, args);
+}
 
 template <typename T>
 int max_coresident_ctas(int L, int nr, bool syncfree, int block_threads, int num_sms) {

@@ -54,6 +54,42 @@ cudaError_t launch_fill_sentinel(T *out, int32_t n, int ld, int nr, DevStatus *s
 template <typename T>
 int max_coresident_ctas(int L, int nr, bool syncfree, int block_threads, int num_sms);
 
+// ---------------------------------------------------------------------------
+// Batched solve: many independent plans in one persistent launch.  Matrix m
+// owns CTAs [cta_begin, cta_begin + cta_count); all CTAs are co-resident, a
+// group solves its matrix synchronisation-free and separates the phases of
+// the refinement with a barrier on its own counter (never a grid barrier).
+constexpr int kBatchMaxIter = 16;
+
+struct BatchMat {
+    SolveData<float> s32;     // FP32 structure (refinement)
+    SolveData<double> s64;    // FP64 structure (direct solve)
+    const int32_t *row_ptr;   // original L for the FP64 residual
+    const int32_t *col;
+    const double *val;
+    const double *b;          // [n, nr] row-major
+    double *x;
+    float *d32;               // scratch [n, nr]
+    double *r64;              // scratch [n, nr]
+    double lnorm;             // |L|_inf
+    int32_t n, nr, R;         // rows, right-hand sides, lanes per row group (pow2 >= nr)
+    int32_t cta_begin, cta_count;
+};
+
+struct BatchCtl {             // per matrix, zeroed before every launch
+    unsigned long long bar;
+    unsigned long long norms[kBatchMaxIter + 1][3];  // |r|, |x| per check; [0][2] = |b|
+    int32_t iters;            // corrections applied
+    int32_t converged;
+};
+
+// ir: FP32 solves + FP64 refinement (plans in SPTRSV_F32_IR precision);
+// otherwise one FP64 solve per matrix.
+cudaError_t launch_batch(const BatchMat *mats, int32_t nmats, BatchCtl *ctl, DevStatus *st,
+                         bool ir, double tol, int max_iter, uint64_t timeout_ns, int block_threads,
+                         int grid, cudaStream_t s);
+int batch_max_coresident(bool ir, int block_threads, int num_sms);
+
 // FP64 residual r = b - L x over the original CSR, with infinity norms of r
 // and x accumulated in st->norms[0], [1]; returns at once when ir_flag is set.
 cudaError_t launch_residual(int32_t n, const int32_t *row_ptr, const int32_t *col,
