@@ -137,6 +137,8 @@ typedef struct {
                                 (valid after a synchronisation) */
     int32_t num_sms;
     int32_t poll_backoff_ns;
+    int32_t chosen_depth;    /* SELECT_COSTMODEL: depth the network picked
+                                (-1 when it did not run) */
     double analyze_ms, transform_ms;
 } sptrsv_info_t;
 
@@ -197,6 +199,49 @@ SPTRSV_API sptrsv_status_t sptrsv_get_transformed(sptrsv_plan_t p, int32_t *d_ne
                                        double *d_xval, int64_t *d_bptr,
                                        int32_t *d_bcol, double *d_bw,
                                        sptrsv_stream_t stream);
+
+/* ---- Learned cost model ----------------------------------------------
+ * The paper picks the rows to rewrite by hand (Sec. IV).  With a network
+ * attached (sptrsv_set_costmodel), SPTRSV_SELECT_COSTMODEL predicts the log
+ * solve time of merging every d+1 levels for d in {0,1,2,3,4,6,8} from 16
+ * features per candidate and keeps the argmin; without one it falls back to
+ * heuristic H.  The network: F -> H -> H -> 1, ReLU, FP32, weights in one
+ * flat array W1[F][H], b1[H], W2[H][H], b2[H], W3[H], b3 (row-major). */
+
+/* Features of the candidate depths (h_feat: [nd][16] floats, host):
+ *  0 log2 n, 1 log2 nnz, 2 dependencies per row, 3 log2 levels,
+ *  4 log2 rows per level, 5-6 fraction of levels with < 32 / < 1024 rows,
+ *  7 fraction of rows in levels of < 1024 rows, 8-11 fraction of rows with
+ *  0 | 1-2 | 3-6 | >= 7 dependencies, 12 d, 13 log2 levels after merging,
+ *  14 FLOPs after / FLOPs before, 15 fraction of rows rewritten.
+ * Fill counts come from the device rewriting kernels; synchronises. */
+SPTRSV_API sptrsv_status_t sptrsv_costmodel_features(sptrsv_plan_t p, const int32_t *h_depths,
+                                                     int32_t nd, float *h_feat,
+                                                     sptrsv_stream_t stream);
+/* Attach (or detach with NULL) a network to a plan; not owned by the plan. */
+SPTRSV_API sptrsv_status_t sptrsv_set_costmodel(sptrsv_plan_t p, sptrsv_mlp_t net);
+
+SPTRSV_API int64_t sptrsv_mlp_num_params(int32_t n_in, int32_t hidden);
+/* New network with the given initial weights (host array). */
+SPTRSV_API sptrsv_status_t sptrsv_mlp_create(int32_t n_in, int32_t hidden,
+                                             const float *h_params, sptrsv_mlp_t *out);
+SPTRSV_API sptrsv_status_t sptrsv_mlp_get_params(sptrsv_mlp_t net, float *h_params);
+/* Input normalisation used by SELECT_COSTMODEL: (f - mean) / std. */
+SPTRSV_API sptrsv_status_t sptrsv_mlp_set_normalization(sptrsv_mlp_t net, const float *h_mean,
+                                                        const float *h_std);
+/* y[N] = network(X[N][F]) on device buffers (inputs already normalised). */
+SPTRSV_API sptrsv_status_t sptrsv_mlp_forward(sptrsv_mlp_t net, const float *d_X, int32_t N,
+                                              float *d_y, sptrsv_stream_t stream);
+/* Gradients of mean((y - t)^2) w.r.t. all weights (flat, d_grads) and the
+ * loss (d_loss); either output may be NULL. */
+SPTRSV_API sptrsv_status_t sptrsv_mlp_grads(sptrsv_mlp_t net, const float *d_X,
+                                            const float *d_target, int32_t N, float *d_grads,
+                                            float *d_loss, sptrsv_stream_t stream);
+/* One full-batch Adam step (beta1 0.9, beta2 0.999, eps 1e-8). */
+SPTRSV_API sptrsv_status_t sptrsv_mlp_train_step(sptrsv_mlp_t net, const float *d_X,
+                                                 const float *d_target, int32_t N, float lr,
+                                                 float *d_loss, sptrsv_stream_t stream);
+SPTRSV_API void sptrsv_mlp_destroy(sptrsv_mlp_t net);
 
 /* Batched solve (the paper treats one matrix; this serves many independent
  * systems of uneven size at once).  All plans must live on the current

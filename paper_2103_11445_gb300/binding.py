@@ -58,6 +58,7 @@ class Info(Structure):
         ("grid_blocks", c_int32), ("cta_run_rows", c_int32),
         ("thin_rows", c_int32), ("max_depth", c_int32), ("flop_budget", c_double),
         ("ir_iters_last", c_int32), ("num_sms", c_int32), ("poll_backoff_ns", c_int32),
+        ("chosen_depth", c_int32),
         ("analyze_ms", c_double), ("transform_ms", c_double),
     ]
 
@@ -85,6 +86,18 @@ _SIGS = {
                                          c_void_p, c_void_p, c_void_p, c_void_p,
                                          c_void_p]),
     "sptrsv_debug_inject_wait": (c_int32, [c_void_p, c_int32]),
+    "sptrsv_costmodel_features": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
+    "sptrsv_set_costmodel": (c_int32, [c_void_p, c_void_p]),
+    "sptrsv_mlp_num_params": (c_int64, [c_int32, c_int32]),
+    "sptrsv_mlp_create": (c_int32, [c_int32, c_int32, c_void_p, POINTER(c_void_p)]),
+    "sptrsv_mlp_get_params": (c_int32, [c_void_p, c_void_p]),
+    "sptrsv_mlp_set_normalization": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "sptrsv_mlp_forward": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
+    "sptrsv_mlp_grads": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p,
+                                   c_void_p]),
+    "sptrsv_mlp_train_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, ctypes.c_float,
+                                        c_void_p, c_void_p]),
+    "sptrsv_mlp_destroy": (None, [c_void_p]),
     "sptrsv_batch_create": (c_int32, [c_void_p, c_int32, POINTER(c_void_p)]),
     "sptrsv_batch_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sptrsv_batch_check": (c_int32, [c_void_p, c_void_p]),
@@ -212,6 +225,70 @@ def sptrsv_last_kernel_ms(plan: int) -> float:
     ms = ctypes.c_float()
     _check(load().sptrsv_last_kernel_ms(plan, byref(ms)), "sptrsv_last_kernel_ms")
     return float(ms.value)
+
+
+def sptrsv_costmodel_features(plan: int, depths, stream: int = 0):
+    import numpy as np
+    d = np.ascontiguousarray(depths, dtype=np.int32)
+    out = np.zeros((d.size, 16), dtype=np.float32)
+    _check(load().sptrsv_costmodel_features(plan, d.ctypes.data, d.size, out.ctypes.data,
+                                            stream), "sptrsv_costmodel_features")
+    return out
+
+
+def sptrsv_set_costmodel(plan: int, mlp: int) -> None:
+    _check(load().sptrsv_set_costmodel(plan, mlp), "sptrsv_set_costmodel")
+
+
+def sptrsv_mlp_num_params(n_in: int, hidden: int) -> int:
+    return int(load().sptrsv_mlp_num_params(n_in, hidden))
+
+
+def sptrsv_mlp_create(n_in: int, hidden: int, params) -> int:
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != sptrsv_mlp_num_params(n_in, hidden):
+        raise ValueError("wrong number of network weights")
+    out = c_void_p()
+    _check(load().sptrsv_mlp_create(n_in, hidden, p.ctypes.data, byref(out)),
+           "sptrsv_mlp_create")
+    return out.value
+
+
+def sptrsv_mlp_get_params(mlp: int, n_in: int, hidden: int):
+    import numpy as np
+    out = np.zeros(sptrsv_mlp_num_params(n_in, hidden), dtype=np.float32)
+    _check(load().sptrsv_mlp_get_params(mlp, out.ctypes.data), "sptrsv_mlp_get_params")
+    return out
+
+
+def sptrsv_mlp_set_normalization(mlp: int, mean, std) -> None:
+    import numpy as np
+    m = np.ascontiguousarray(mean, dtype=np.float32)
+    s = np.ascontiguousarray(std, dtype=np.float32)
+    _check(load().sptrsv_mlp_set_normalization(mlp, m.ctypes.data, s.ctypes.data),
+           "sptrsv_mlp_set_normalization")
+
+
+def sptrsv_mlp_forward(mlp: int, d_X: int, N: int, d_y: int, stream: int = 0) -> None:
+    _check(load().sptrsv_mlp_forward(mlp, d_X, N, d_y, stream), "sptrsv_mlp_forward")
+
+
+def sptrsv_mlp_grads(mlp: int, d_X: int, d_t: int, N: int, d_grads: int, d_loss: int,
+                     stream: int = 0) -> None:
+    _check(load().sptrsv_mlp_grads(mlp, d_X, d_t, N, d_grads, d_loss, stream),
+           "sptrsv_mlp_grads")
+
+
+def sptrsv_mlp_train_step(mlp: int, d_X: int, d_t: int, N: int, lr: float, d_loss: int,
+                          stream: int = 0) -> None:
+    _check(load().sptrsv_mlp_train_step(mlp, d_X, d_t, N, lr, d_loss, stream),
+           "sptrsv_mlp_train_step")
+
+
+def sptrsv_mlp_destroy(mlp: int) -> None:
+    if mlp:
+        load().sptrsv_mlp_destroy(mlp)
 
 
 def sptrsv_batch_create(plans) -> int:

@@ -1,0 +1,237 @@
+"""Learned choice of the rewriting depth.
+
+The paper chooses the rows to rewrite by hand (Sec. IV).  Here a small network
+(``libsptrsv`` cost-model kernels: 16 features -> 64 -> 64 -> 1, ReLU, FP32,
+trained with Adam on the GPU) predicts the log solve time of "merge every
+d+1 levels" for d in DEPTHS, and ``SPTRSV_SELECT_COSTMODEL`` keeps the argmin.
+Heuristic H remains the fallback when no network is attached, and the
+baseline the network is judged against.
+
+Training data come from the solver itself: for every seeded synthetic matrix
+(``matgen`` mixtures) and every depth, the library's features of that
+candidate and the measured time of the library's own solve of the rewritten
+plan (median of a few solves, L2 flushed before each).
+
+    python -m paper_2103_11445_gb300.costmodel collect --count 600 --out data.npz
+    python -m paper_2103_11445_gb300.costmodel train --data data.npz --out weights.npz
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import statistics
+import sys
+import time
+
+import numpy as np
+
+from . import binding as B
+
+DEPTHS = (0, 1, 2, 3, 4, 6, 8)
+N_FEATURES = 16
+HIDDEN = 64
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "costmodel_weights.npz")
+# launch shape used for the timing labels and for the model's own plans
+LABEL_LAUNCH = dict(solve_mode=B.SOLVE_SYNCFREE, block_threads=128, lanes_per_row=0)
+
+
+def init_params(n_in: int = N_FEATURES, hidden: int = HIDDEN, seed: int = 0) -> np.ndarray:
+    """He-uniform weights, zero biases, in the library's flat layout."""
+    rng = np.random.default_rng(seed)
+
+    def he(fan_in, shape):
+        lim = np.sqrt(6.0 / fan_in)
+        return rng.uniform(-lim, lim, shape)
+
+    parts = [he(n_in, (n_in, hidden)), np.zeros(hidden), he(hidden, (hidden, hidden)),
+             np.zeros(hidden), he(hidden, (hidden, 1)), np.zeros(1)]
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+
+class CostModel:
+    """A cost-model network living on the current CUDA device."""
+
+    def __init__(self, params: np.ndarray | None = None, mean=None, std=None,
+                 n_in: int = N_FEATURES, hidden: int = HIDDEN, seed: int = 0):
+        self.n_in, self.hidden = n_in, hidden
+        if params is None:
+            params = init_params(n_in, hidden, seed)
+        self.handle = B.sptrsv_mlp_create(n_in, hidden, params)
+        self.mean = np.zeros(n_in, np.float32) if mean is None else np.asarray(mean, np.float32)
+        self.std = np.ones(n_in, np.float32) if std is None else np.asarray(std, np.float32)
+        B.sptrsv_mlp_set_normalization(self.handle, self.mean, self.std)
+
+    # -- training ----------------------------------------------------------
+    def fit(self, X: np.ndarray, y: np.ndarray, epochs: int = 3000, lr: float = 3e-3,
+            log_every: int = 0) -> list:
+        """Full-batch Adam on normalised features (statistics from X)."""
+        import torch
+        self.mean = X.mean(axis=0).astype(np.float32)
+        self.std = np.where(X.std(axis=0) > 1e-6, X.std(axis=0), 1.0).astype(np.float32)
+        B.sptrsv_mlp_set_normalization(self.handle, self.mean, self.std)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        Xn = torch.as_tensor((X - self.mean) / self.std, dtype=torch.float32, device=dev)
+        t = torch.as_tensor(y, dtype=torch.float32, device=dev)
+        loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        stream = torch.cuda.current_stream().cuda_stream
+        hist = []
+        for e in range(epochs):
+            B.sptrsv_mlp_train_step(self.handle, Xn.data_ptr(), t.data_ptr(), Xn.shape[0], lr,
+                                    loss.data_ptr(), stream)
+            if log_every and (e % log_every == 0 or e == epochs - 1):
+                hist.append((e, float(loss.item())))
+        return hist
+
+    def predict(self, X: np.ndarray) -> np.ndarray:
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        Xn = torch.as_tensor((np.asarray(X) - self.mean) / self.std, dtype=torch.float32,
+                             device=dev)
+        y = torch.empty(Xn.shape[0], dtype=torch.float32, device=dev)
+        B.sptrsv_mlp_forward(self.handle, Xn.data_ptr(), Xn.shape[0], y.data_ptr(),
+                             torch.cuda.current_stream().cuda_stream)
+        return y.cpu().numpy()
+
+    def params(self) -> np.ndarray:
+        return B.sptrsv_mlp_get_params(self.handle, self.n_in, self.hidden)
+
+    # -- persistence ------------------------------------------------------------
+    def save(self, path: str = WEIGHTS) -> None:
+        np.savez(path, params=self.params(), mean=self.mean, std=self.std,
+                 n_in=self.n_in, hidden=self.hidden, depths=np.array(DEPTHS))
+
+    @classmethod
+    def load(cls, path: str = WEIGHTS) -> "CostModel":
+        d = np.load(path)
+        return cls(d["params"], d["mean"], d["std"], int(d["n_in"]), int(d["hidden"]))
+
+    def attach(self, plan: "B.Plan") -> None:
+        B.sptrsv_set_costmodel(plan.handle, self.handle)
+
+    def close(self) -> None:
+        if self.handle:
+            B.sptrsv_mlp_destroy(self.handle)
+            self.handle = 0
+
+
+# --- data ------------------------------------------------------------------------
+
+def time_solves(plan: "B.Plan", n: int, reps: int = 5) -> float:
+    """Median solve time in microseconds, L2 flushed before each solve."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    b = torch.ones(n, dtype=torch.float64, device=dev)
+    x = torch.empty_like(b)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    plan.solve(b, x)
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.solve(b, x)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e3)
+    plan.check()
+    return statistics.median(ts)
+
+
+def heuristic_time(plan: "B.Plan", n: int, reps: int = 5) -> float:
+    plan.transform(select_mode=B.SELECT_HEURISTIC, **LABEL_LAUNCH)
+    return time_solves(plan, n, reps)
+
+
+def collect(specs, reps: int = 5, with_heuristic: bool = True, log=None):
+    """Features and measured log2 times (us) for every spec and depth."""
+    import matgen as mg
+    X, y, group, hs = [], [], [], []
+    for k, sp in enumerate(specs):
+        A = mg.make_from_spec(sp)
+        P = B.Plan(A.n, A.row_ptr, A.col, A.val)
+        feats = B.sptrsv_costmodel_features(P.handle, DEPTHS)
+        for d, f in zip(DEPTHS, feats):
+            kw = dict(select_mode=B.SELECT_FIXED, depth=d) if d else \
+                dict(select_mode=B.SELECT_NONE)
+            P.transform(**kw, **LABEL_LAUNCH)
+            us = time_solves(P, A.n, reps)
+            X.append(f)
+            y.append(np.log2(us))
+            group.append(k)
+        hs.append(np.log2(heuristic_time(P, A.n, reps)) if with_heuristic else np.nan)
+        P.close()
+        if log and (k % 20 == 0 or k == len(specs) - 1):
+            log(f"collected {k + 1}/{len(specs)} (n={A.n})")
+    return (np.asarray(X, np.float32), np.asarray(y, np.float32), np.asarray(group, np.int32),
+            np.asarray(hs, np.float32))
+
+
+def regret(model: CostModel, X, y, group, h_times):
+    """Per matrix: time of the network's pick, of the best depth and of H."""
+    rows = []
+    pred = model.predict(X)
+    for g in np.unique(group):
+        sel = group == g
+        yt, yp = y[sel], pred[sel]
+        rows.append((2.0 ** yt[np.argmin(yp)], 2.0 ** yt.min(), 2.0 ** h_times[g],
+                     2.0 ** yt[0]))
+    r = np.asarray(rows)
+    return dict(
+        mean_regret=float(np.mean(r[:, 0] / r[:, 1])),
+        geo_speedup_vs_heuristic=float(np.exp(np.mean(np.log(r[:, 2] / r[:, 0])))),
+        geo_speedup_vs_plain=float(np.exp(np.mean(np.log(r[:, 3] / r[:, 0])))),
+        geo_speedup_best_vs_heuristic=float(np.exp(np.mean(np.log(r[:, 2] / r[:, 1])))),
+        picks_best=float(np.mean(r[:, 0] <= r[:, 1] * 1.0001)),
+        matrices=int(r.shape[0]))
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(prog="costmodel")
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    c = sub.add_parser("collect")
+    c.add_argument("--count", type=int, default=600)
+    c.add_argument("--seed", type=int, default=5000)
+    c.add_argument("--n-hi", type=float, default=5e5)
+    c.add_argument("--reps", type=int, default=5)
+    c.add_argument("--out", required=True)
+    t = sub.add_parser("train")
+    t.add_argument("--data", required=True)
+    t.add_argument("--out", default=WEIGHTS)
+    t.add_argument("--train-frac", type=float, default=0.8)
+    t.add_argument("--epochs", type=int, default=4000)
+    t.add_argument("--lr", type=float, default=3e-3)
+    args = ap.parse_args(argv)
+    import torch
+    torch.cuda.set_device(0)
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import matgen as mg
+    if args.cmd == "collect":
+        specs = mg.batch_specs(args.count, seed=args.seed, n_lo=1e4, n_hi=args.n_hi,
+                               nrhs_max=1, band_range=(5, 20))
+        t0 = time.time()
+        X, y, g, h = collect(specs, reps=args.reps, log=lambda s: print(s, flush=True))
+        np.savez(args.out, X=X, y=y, group=g, h=h, depths=np.array(DEPTHS),
+                 specs=np.array([str(s) for s in specs]))
+        print(f"collected {len(specs)} matrices in {time.time() - t0:.1f} s")
+        return 0
+    d = np.load(args.data)
+    X, y, g, h = d["X"], d["y"], d["group"], d["h"]
+    ng = int(g.max()) + 1
+    cut = int(round(ng * args.train_frac))
+    tr, te = g < cut, g >= cut
+    m = CostModel()
+    hist = m.fit(X[tr], y[tr], epochs=args.epochs, lr=args.lr, log_every=500)
+    for e, l in hist:
+        print(f"epoch {e}: train mse {l:.4f}")
+    te_mse = float(np.mean((m.predict(X[te]) - y[te]) ** 2))
+    gt = g[te] - cut
+    res = regret(m, X[te], y[te], gt, h[cut:])
+    res["test_mse_log2"] = te_mse
+    print(res)
+    m.save(args.out)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

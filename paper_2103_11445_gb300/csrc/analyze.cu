@@ -210,6 +210,21 @@ radix_scatter(const uint32_t *__restrict__ keys_in, const int32_t *__restrict__ 
     }
 }
 
+// rows by off-diagonal count: 0 | 1-2 | 3-6 | >= 7
+__global__ void offdeg_hist_kernel(int32_t n, const int32_t *__restrict__ offdeg,
+                                   unsigned long long *bins) {
+    __shared__ unsigned long long h[4];
+    if (threadIdx.x < 4) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = offdeg[i];
+        atomicAdd(&h[d == 0 ? 0 : d <= 2 ? 1 : d <= 6 ? 2 : 3], 1ull);
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) atomicAdd(&bins[threadIdx.x], h[threadIdx.x]);
+}
+
 __global__ void iota_kernel(int32_t *v, int32_t n) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) v[i] = i;
@@ -261,6 +276,15 @@ cudaError_t launch_bfs_levels(int32_t n, const int32_t *tptr, const int32_t *tid
                     (void *)&nlev_out, (void *)&st, (void *)&timeout_ns};
     return cudaLaunchCooperativeKernel((void *)bfs_levels_kernel, dim3(grid),
                                        dim3(kBfsThreads), args, 0, s);
+}
+
+cudaError_t launch_offdeg_hist(int32_t n, const int32_t *offdeg, unsigned long long *bins,
+                               cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    int64_t blocks = ((int64_t)n + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    offdeg_hist_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, offdeg, bins);
+    return cudaGetLastError();
 }
 
 size_t radix_tmp_bytes(int32_t n) {

@@ -13,6 +13,12 @@
 
 using namespace sptrsv;
 
+namespace sptrsv {
+// mlp.cu: normalise h_feat [count][16] and run the network, h_pred[count]
+sptrsv_status_t costmodel_predict(sptrsv_mlp_t net, const float *h_feat, int count,
+                                  float *h_pred, cudaStream_t s);
+}
+
 namespace {
 
 sptrsv_status_t cuda_status(cudaError_t e) {
@@ -163,35 +169,15 @@ struct FillOracle {
 
 int64_t plain_flops(const sptrsv_plan_s *p) { return 2 * (p->nnz - p->n) + p->n; }
 
-sptrsv_status_t choose_segments(sptrsv_plan_t p, cudaStream_t s) {
-    const auto &prm = p->prm;
+// Segments chosen by H for (tau, d_max, rho), with the FLOPs they add;
+// leaves the plan untouched.
+sptrsv_status_t compute_segments(sptrsv_plan_t p, int64_t tau, int32_t d_max, double rho,
+                                 cudaStream_t s, std::vector<std::pair<int32_t, int32_t>> *out,
+                                 int64_t *added_flops) {
     const int32_t nlev = p->nlev;
-    p->seg_first.clear();
-    p->seg_depth.clear();
-    if (prm.select_mode == SPTRSV_SELECT_NONE || nlev == 0) {
-        for (int32_t l = 0; l < nlev; ++l) {
-            p->seg_first.push_back(l);
-            p->seg_depth.push_back(0);
-        }
-        return SPTRSV_OK;
-    }
-    int64_t tau;
-    int32_t d_max;
-    double rho;
-    if (prm.select_mode == SPTRSV_SELECT_FIXED) {
-        tau = INT64_MAX;
-        d_max = prm.depth;
-        rho = INFINITY;
-    } else if (prm.select_mode == SPTRSV_SELECT_HEURISTIC) {
-        tau = prm.thin_rows;
-        d_max = prm.max_depth;
-        rho = prm.flop_budget;
-    } else {
-        return SPTRSV_ERR_UNSUPPORTED;
-    }
     std::vector<int64_t> rows(nlev);
     for (int32_t l = 0; l < nlev; ++l) rows[l] = p->h_level_ptr[l + 1] - p->h_level_ptr[l];
-    FillOracle fo{p, s, prm.max_row_fill};
+    FillOracle fo{p, s, p->prm.max_row_fill};
     // speculative batch: the uncut path plus every first step after a cut
     std::vector<std::pair<int32_t, int32_t>> qs;
     fo.optimistic_from(0, rows, tau, d_max, qs);
@@ -213,8 +199,114 @@ sptrsv_status_t choose_segments(sptrsv_plan_t p, cudaStream_t s) {
         *cost = it->second;
         return true;
     };
-    auto segs = select_segments(rows, tau, d_max, rho, plain_flops(p), added);
+    *out = select_segments(rows, tau, d_max, rho, plain_flops(p), added);
     if (fo.err != SPTRSV_OK) return fo.err;
+    int64_t tot = 0;
+    for (auto &sg : *out)
+        for (int32_t r = 1; r <= sg.second; ++r) tot += fo.cache[{sg.first + r, r}];
+    *added_flops = tot;
+    return SPTRSV_OK;
+}
+
+// Candidate rewrite depths the cost model chooses from (0 = plain levels).
+constexpr int kCostDepths[] = {0, 1, 2, 3, 4, 6, 8};
+constexpr int kNumCostDepths = 7;
+constexpr int kCostFeatures = 16;
+
+// Features of "merge every d+1 levels" on this plan (the analysis features
+// of the matrix-analysis module, Sec. IV, plus the candidate's fill):
+//  0 log2 n, 1 log2 nnz, 2 dependencies per row, 3 log2 levels,
+//  4 log2 rows per level, 5-6 fraction of levels with < 32 / < 1024 rows,
+//  7 fraction of rows in levels of < 1024 rows, 8-11 fraction of rows with
+//  0 | 1-2 | 3-6 | >= 7 dependencies, 12 d, 13 log2 levels after,
+//  14 FLOPs after / FLOPs before, 15 fraction of rows rewritten.
+sptrsv_status_t candidate_features(sptrsv_plan_t p, int d, float *f, cudaStream_t s) {
+    const double n = std::max<int32_t>(p->n, 1), nnz = std::max<int64_t>(p->nnz, 1);
+    const int32_t nlev = std::max<int32_t>(p->nlev, 1);
+    int64_t thin32 = 0, thin1k = 0, rows1k = 0;
+    for (int32_t l = 0; l < p->nlev; ++l) {
+        const int64_t r = p->h_level_ptr[l + 1] - p->h_level_ptr[l];
+        thin32 += r < 32;
+        thin1k += r < 1024;
+        rows1k += r < 1024 ? r : 0;
+    }
+    std::vector<std::pair<int32_t, int32_t>> segs;
+    int64_t added = 0;
+    if (d > 0 && p->nlev > 0) {
+        CKS(compute_segments(p, INT64_MAX, d, INFINITY, s, &segs, &added));
+    } else {
+        for (int32_t l = 0; l < p->nlev; ++l) segs.emplace_back(l, 0);
+    }
+    int64_t rewritten = 0;
+    for (auto &sg : segs)
+        rewritten += p->h_level_ptr[sg.first + sg.second + 1] - p->h_level_ptr[sg.first + 1];
+    const double fp = (double)std::max<int64_t>(plain_flops(p), 1);
+    f[0] = (float)std::log2(n);
+    f[1] = (float)std::log2(nnz);
+    f[2] = (float)((p->nnz - p->n) / n);
+    f[3] = (float)std::log2((double)nlev);
+    f[4] = (float)std::log2(n / nlev);
+    f[5] = (float)thin32 / nlev;
+    f[6] = (float)thin1k / nlev;
+    f[7] = (float)(rows1k / n);
+    for (int k = 0; k < 4; ++k) f[8 + k] = (float)(p->offdeg_hist[k] / n);
+    f[12] = (float)d;
+    f[13] = (float)std::log2((double)std::max<size_t>(segs.size(), 1));
+    f[14] = (float)((fp + added) / fp);
+    f[15] = (float)(rewritten / n);
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t choose_segments(sptrsv_plan_t p, cudaStream_t s) {
+    const auto &prm = p->prm;
+    const int32_t nlev = p->nlev;
+    p->seg_first.clear();
+    p->seg_depth.clear();
+    p->chosen_depth = -1;
+    if (prm.select_mode == SPTRSV_SELECT_NONE || nlev == 0) {
+        for (int32_t l = 0; l < nlev; ++l) {
+            p->seg_first.push_back(l);
+            p->seg_depth.push_back(0);
+        }
+        return SPTRSV_OK;
+    }
+    int64_t tau;
+    int32_t d_max;
+    double rho;
+    if (prm.select_mode == SPTRSV_SELECT_COSTMODEL && p->costmodel) {
+        // the network predicts the log solve time of every candidate depth
+        float feat[kNumCostDepths * kCostFeatures];
+        for (int i = 0; i < kNumCostDepths; ++i)
+            CKS(candidate_features(p, kCostDepths[i], feat + i * kCostFeatures, s));
+        float pred[kNumCostDepths];
+        CKS(costmodel_predict(p->costmodel, feat, kNumCostDepths, pred, s));
+        int best = 0;
+        for (int i = 1; i < kNumCostDepths; ++i)
+            if (pred[i] < pred[best]) best = i;
+        p->chosen_depth = kCostDepths[best];
+        tau = INT64_MAX;
+        d_max = kCostDepths[best];
+        rho = INFINITY;
+    } else if (prm.select_mode == SPTRSV_SELECT_FIXED) {
+        tau = INT64_MAX;
+        d_max = prm.depth;
+        rho = INFINITY;
+    } else if (prm.select_mode == SPTRSV_SELECT_HEURISTIC ||
+               prm.select_mode == SPTRSV_SELECT_COSTMODEL) {
+        // heuristic H, also the fallback when no cost model is attached
+        tau = prm.thin_rows;
+        d_max = prm.max_depth;
+        rho = prm.flop_budget;
+    } else {
+        return SPTRSV_ERR_UNSUPPORTED;
+    }
+    std::vector<std::pair<int32_t, int32_t>> segs;
+    int64_t added = 0;
+    if (d_max == 0) {
+        for (int32_t l = 0; l < nlev; ++l) segs.emplace_back(l, 0);
+    } else {
+        CKS(compute_segments(p, tau, d_max, rho, s, &segs, &added));
+    }
     for (auto &sg : segs) {
         p->seg_first.push_back(sg.first);
         p->seg_depth.push_back(sg.second);
@@ -710,6 +802,16 @@ sptrsv_status_t sptrsv_analyze(int32_t n, int64_t nnz, const int32_t *d_row_ptr,
     CKP(cudaMemcpyAsync(&h_err, err.p, sizeof(h_err), cudaMemcpyDeviceToHost, s));
     CKP(cudaStreamSynchronize(s));
     if (h_err != ~0ull) return fail((sptrsv_status_t)(h_err & 0xff));
+    {
+        DevArr<unsigned long long> bins;
+        CKP(bins.alloc(4));
+        CKP(cudaMemsetAsync(bins.p, 0, 4 * sizeof(unsigned long long), s));
+        CKP(launch_offdeg_hist(n, p->offdeg.p, bins.p, s));
+        unsigned long long hb[4];
+        CKP(cudaMemcpyAsync(hb, bins.p, sizeof(hb), cudaMemcpyDeviceToHost, s));
+        CKP(cudaStreamSynchronize(s));
+        for (int k = 0; k < 4; ++k) p->offdeg_hist[k] = (int64_t)hb[k];
+    }
     // successor lists (transpose of the strict lower part)
     const int64_t nsucc = nnz - n;
     DevArr<int32_t> tcnt, tptr, tcur, tidx;
@@ -870,6 +972,7 @@ sptrsv_status_t sptrsv_get_info(sptrsv_plan_t p, sptrsv_info_t *o) {
     o->flop_budget = p->prm.flop_budget;
     o->num_sms = p->num_sms;
     o->poll_backoff_ns = p->cfg.backoff_ns;
+    o->chosen_depth = p->chosen_depth;
     o->analyze_ms = p->analyze_ms;
     o->transform_ms = p->transform_ms;
     if (p->status.p) {
@@ -946,6 +1049,24 @@ sptrsv_status_t sptrsv_get_transformed(sptrsv_plan_t p, int32_t *d_new_level, in
                           p->s64.row_id.p, p->s64.chunk_level.p, xptr, bptr, d_xcol, d_xval,
                           d_bcol, d_bw, d_new_level, s));
     CK(cudaStreamSynchronize(s));
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_set_costmodel(sptrsv_plan_t p, sptrsv_mlp_t net) {
+    if (!p) return SPTRSV_ERR_INVALID_ARG;
+    p->costmodel = net;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_costmodel_features(sptrsv_plan_t p, const int32_t *h_depths, int32_t nd,
+                                          float *h_feat, sptrsv_stream_t stream) {
+    if (!p || nd < 0 || (nd > 0 && (!h_depths || !h_feat))) return SPTRSV_ERR_INVALID_ARG;
+    if (p->latched != SPTRSV_OK) return SPTRSV_ERR_BAD_STATE;
+    for (int32_t i = 0; i < nd; ++i) {
+        if (h_depths[i] < 0 || h_depths[i] > 16) return SPTRSV_ERR_INVALID_ARG;
+        CKS(candidate_features(p, h_depths[i], h_feat + (int64_t)i * kCostFeatures,
+                               (cudaStream_t)stream));
+    }
     return SPTRSV_OK;
 }
 

@@ -42,6 +42,9 @@ cudaError_t launch_bfs_levels(int32_t n, const int32_t *tptr, const int32_t *tid
                               int32_t *cnt3, int32_t *level_start,
                               int32_t *nlev_out, DevStatus *st,
                               uint64_t timeout_ns, int num_sms, cudaStream_t s);
+// histogram of rows by off-diagonal count (bins 0 | 1-2 | 3-6 | >= 7)
+cudaError_t launch_offdeg_hist(int32_t n, const int32_t *offdeg, unsigned long long *bins,
+                               cudaStream_t s);
 // perm = rows ordered by (level, row), via a stable LSD radix sort.
 // tmp must hold radix_tmp_bytes(n) bytes.
 size_t radix_tmp_bytes(int32_t n);

@@ -98,6 +98,7 @@ struct sptrsv_plan_s {
     sptrsv::DevArr<int32_t> offdeg, level, level_ptr, perm;
     std::vector<int32_t> h_level_ptr;
     int32_t nlev = 0;
+    int64_t offdeg_hist[4] = {0, 0, 0, 0};   // rows with 0 | 1-2 | 3-6 | >= 7 dependencies
     sptrsv::DevArr<sptrsv::DevStatus> status;
     sptrsv::DevArr<unsigned long long> lnorm;
     // transform
@@ -119,6 +120,7 @@ struct sptrsv_plan_s {
     int32_t thin_rows_used = 0;
     sptrsv_status_t latched = SPTRSV_OK;
     sptrsv_mlp_t costmodel = nullptr;  // not owned
+    int32_t chosen_depth = -1;         // depth picked by the cost model (-1: none)
     // profiling: events around the main solve kernel of the last solve
     bool profiling = false;
     cudaEvent_t prof_ev[2] = {nullptr, nullptr};
