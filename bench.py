@@ -31,7 +31,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "stencil3d_128"
+WORKLOAD = "stencil3d_128"  # the workload the committed ncu summaries were taken on
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--side", type=int, default=128, help="grid side of the 3D stencil")
+    ap.add_argument("--workload", choices=["stencil3d", "thin_tail"], default="stencil3d",
+                    help="stencil3d: the 3D 7-point lower triangle (default); thin_tail: the "
+                         "1M-row random-banded matrix with a near-serial 50k-row tail")
     ap.add_argument("--depths", default="1,2,3,4,6",
                     help="fixed rewrite depths tried besides heuristic H")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -61,11 +64,22 @@ def parse():
     return ap.parse_args()
 
 
-def workload(side: int):
+def workload(side: int, kind: str = "stencil3d"):
     import matgen as mg
+    if kind == "thin_tail":
+        A = mg.thin_tail(1_000_000, seed=3000)
+        return A, mg.rhs_uniform(A.n, seed=3001)
     A = mg.stencil3d(side, seed=2000)
     b = mg.rhs_uniform(A.n, seed=2001)
     return A, b
+
+
+def workload_name(args, A) -> str:
+    if args.workload == "thin_tail":
+        return (f"thin_tail_1m (950k random-banded rows, 8 deps in a 2000-row band, then a "
+                f"50k-row near-serial chain; n={A.n}, nnz={A.nnz}, 1 RHS b~U[-1,1])")
+    return (f"stencil3d_{args.side} (3D 7-point Laplacian lower triangle, n={A.n}, "
+            f"nnz={A.nnz}, diag 6+U[0,0.1], 1 RHS b~U[-1,1])")
 
 
 def peaks():
@@ -208,7 +222,7 @@ def oracle_solve_timed(A, b, seconds: float, min_runs: int = 3, max_runs: int = 
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
-    A, b = workload(args.side)
+    A, b = workload(args.side, args.workload)
     import oracle
     oracle.build()
     for _ in range(max(args.warmup, 0)):
@@ -226,8 +240,7 @@ def run_reference(args, world, rank):
         "value": round(val, 4), "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"stencil3d_{args.side} (3D 7-point lower triangle, n={A.n}, "
-                               f"nnz={A.nnz}, 1 RHS)", "b_alg_bytes": B},
+        "config": {"workload": workload_name(args, A), "b_alg_bytes": B},
         "cpu_baseline": {"value": round(val, 4), "unit": "GB/s", "cores": 1,
                          "kind": "oracle",
                          "sample": f"{args.steps} full serial FP64 forward substitutions "
@@ -255,7 +268,7 @@ def run_profile(args):
     import torch
     from paper_2103_11445_gb300 import binding as Bd
     dev = torch.device("cuda", torch.cuda.current_device())
-    A, b_np = workload(args.side)
+    A, b_np = workload(args.side, args.workload)
     P = Bd.Plan(A.n, A.row_ptr, A.col, A.val)
     mode = Bd.SOLVE_SYNCFREE if args.mode == "syncfree" else Bd.SOLVE_BARRIER
     P.transform(solve_mode=mode, lanes_per_row=args.lanes, block_threads=args.block,
@@ -287,7 +300,7 @@ def run_ours(args, world, rank, local):
     from paper_2103_11445_gb300 import binding as Bd
 
     dev = torch.device("cuda", torch.cuda.current_device())
-    A, b_np = workload(args.side)
+    A, b_np = workload(args.side, args.workload)
     n, nnz = A.n, A.nnz
     B = b_alg(n, nnz)
     rp = torch.as_tensor(A.row_ptr, device=dev)
@@ -344,6 +357,27 @@ def run_ours(args, world, rank, local):
                              solve_mode=info["solve_mode"], L=info["lanes_per_row"],
                              block=info["block_threads"], grid=info["grid_blocks"],
                              cta_run_rows=info["cta_run_rows"])
+    # the learned cost model's own pick (weights trained on the solver's timings)
+    cm_info = None
+    try:
+        from paper_2103_11445_gb300 import costmodel as cmod
+        if os.path.exists(cmod.WEIGHTS):
+            net = cmod.CostModel.load()
+            net.attach(P)
+            t0 = time.perf_counter()
+            P.transform(select_mode=Bd.SELECT_COSTMODEL, solve_mode=Bd.SOLVE_AUTO)
+            tr_ms = (time.perf_counter() - t0) * 1e3
+            ts, _ = timed(5)
+            info = P.info()
+            cm_info = dict(depth=info["chosen_depth"], ms=statistics.median(ts))
+            results["costmodel"] = dict(ms=statistics.median(ts), transform_ms=tr_ms,
+                                        kw=dict(select_mode=Bd.SELECT_COSTMODEL),
+                                        nlev_new=info["nlev_new"], flops_new=info["flops_new"],
+                                        solve_mode=info["solve_mode"], L=info["lanes_per_row"],
+                                        block=info["block_threads"], grid=info["grid_blocks"],
+                                        cta_run_rows=info["cta_run_rows"])
+    except Exception as exc:  # the weights are optional; report why they were not used
+        cm_info = dict(error=str(exc)[:200])
     rewritten = {k: v for k, v in results.items() if k != "plain"}
     best = min(rewritten, key=lambda k: rewritten[k]["ms"])
 
@@ -404,8 +438,7 @@ def run_ours(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {
-            "workload": f"stencil3d_{args.side} (3D 7-point Laplacian lower triangle, n={n}, "
-                        f"nnz={nnz}, diag 6+U[0,0.1], 1 RHS b~U[-1,1])",
+            "workload": workload_name(args, A),
             "b_alg_bytes": B, "levels": nlev, "levels_after": info["nlev_new"],
             "selection": best, "solve_mode": "syncfree" if launches_per_solve == 2 else "barrier",
             "lanes_per_row": info["lanes_per_row"], "block_threads": info["block_threads"],
@@ -423,6 +456,7 @@ def run_ours(args, world, rank, local):
             "lanes_per_row": pinfo["lanes_per_row"], "cta_run_rows": pinfo["cta_run_rows"],
         },
         "speedup_vs_plain": round(plain_ms / ms, 3),
+        "costmodel_pick": cm_info,
         "candidates": {k: {"ms": round(v["ms"], 4), "levels": v["nlev_new"],
                            "flops": v["flops_new"],
                            "mode": "syncfree" if v["solve_mode"] == 2 else "barrier",

@@ -15,7 +15,8 @@ TOL64 = 1e-10   # relerr bound for FP64 results
 TOL32 = 1e-5    # relerr bound for unrefined FP32 results
 
 B_MODES = [dict(solve_mode=1, cta_run_rows=-1), dict(solve_mode=1, cta_run_rows=0),
-           dict(solve_mode=2)]
+           dict(solve_mode=2, die_split=0), dict(solve_mode=2, die_split=1)]
+B_IDS = ["barrier", "barrier_runs", "syncfree", "syncfree_dies"]
 
 
 def plain(**kw):
@@ -24,7 +25,7 @@ def plain(**kw):
     return d
 
 
-@pytest.mark.parametrize("mode", B_MODES, ids=["barrier", "barrier_runs", "syncfree"])
+@pytest.mark.parametrize("mode", B_MODES, ids=B_IDS)
 @pytest.mark.parametrize("L", [1, 2, 4, 8, 32])
 def test_modes_and_layouts(mode, L):
     A = mg.thin_tail(20_000, seed=3)
@@ -33,7 +34,7 @@ def test_modes_and_layouts(mode, L):
     assert_close_to_oracle(A, gpu_solve(P, b), b, TOL64)
 
 
-@pytest.mark.parametrize("mode", B_MODES, ids=["barrier", "barrier_runs", "syncfree"])
+@pytest.mark.parametrize("mode", B_MODES, ids=B_IDS)
 @pytest.mark.parametrize("nrhs", [2, 3, 8, 32, 33, 40])
 def test_multi_rhs(mode, nrhs):
     A = mg.stencil3d(12, seed=4)
@@ -44,7 +45,7 @@ def test_multi_rhs(mode, nrhs):
     assert_close_to_oracle(A, x, b, TOL64)
 
 
-@pytest.mark.parametrize("mode", B_MODES, ids=["barrier", "barrier_runs", "syncfree"])
+@pytest.mark.parametrize("mode", B_MODES, ids=B_IDS)
 def test_closed_forms(mode):
     n = 3000
     ident = mg.CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.ones(n))
@@ -58,7 +59,7 @@ def test_closed_forms(mode):
     assert np.array_equal(x, np.arange(1, n + 1, dtype=np.float64))
 
 
-@pytest.mark.parametrize("mode", B_MODES, ids=["barrier", "barrier_runs", "syncfree"])
+@pytest.mark.parametrize("mode", B_MODES, ids=B_IDS)
 def test_diagonal_division_is_correctly_rounded(mode):
     """x_i = b_i / d_i must be the IEEE quotient bit for bit over the whole
     exponent range, zeros, subnormals, infinities and NaN included."""
@@ -77,7 +78,7 @@ def test_diagonal_division_is_correctly_rounded(mode):
     assert same.all(), np.nonzero(~same)[0][:10]
 
 
-@pytest.mark.parametrize("mode", B_MODES, ids=["barrier", "barrier_runs", "syncfree"])
+@pytest.mark.parametrize("mode", B_MODES, ids=B_IDS)
 def test_random_small_matrices(mode):
     for seed in range(4):
         A = mg.random_lower(257, seed=seed, density=0.08)
@@ -100,14 +101,14 @@ def test_single_row_and_long_rows():
             assert_close_to_oracle(A, x, b, TOL64)
 
 
-@pytest.mark.parametrize("mode", B_MODES, ids=["barrier", "barrier_runs", "syncfree"])
+@pytest.mark.parametrize("mode", B_MODES, ids=B_IDS)
 def test_full_stencil3d_128(mode):
     A = mg.stencil3d(128, seed=2000)
     b = mg.rhs_uniform(A.n, seed=2001)
     assert_close_to_oracle(A, gpu_solve(plan_for(A, **plain(**mode)), b), b, TOL64)
 
 
-@pytest.mark.parametrize("mode", B_MODES, ids=["barrier", "barrier_runs", "syncfree"])
+@pytest.mark.parametrize("mode", B_MODES, ids=B_IDS)
 def test_full_thin_tail(mode):
     A = mg.thin_tail(1_000_000, seed=3000)
     b = mg.rhs_uniform(A.n, seed=3001)
