@@ -116,10 +116,6 @@ typedef struct {
     int32_t poll_backoff_ns; /* synchronisation-free solve: sleep between
                                 polls of an unready unknown; 0 = none,
                                 < 0 = auto */
-    int32_t die_split;       /* synchronisation-free solve: 1 = the CTAs on each
-                                die of the GPU take one half of every level
-                                (dependency hops stay on one die), 0 = all
-                                CTAs share every level, < 0 = auto */
 } sptrsv_transform_params_t;
 
 /* Everything a caller may want to report about a plan. */
@@ -143,7 +139,6 @@ typedef struct {
     int32_t poll_backoff_ns;
     int32_t chosen_depth;    /* SELECT_COSTMODEL: depth the network picked
                                 (-1 when it did not run) */
-    int32_t die_split;       /* schedule in use (1 = per-die halves) */
     double analyze_ms, transform_ms;
 } sptrsv_info_t;
 

@@ -44,7 +44,7 @@ class TransformParams(Structure):
         ("precision", c_int32), ("ir_tol", c_double), ("ir_max_iter", c_int32),
         ("lanes_per_row", c_int32), ("block_threads", c_int32),
         ("cta_run_rows", c_int32), ("wait_timeout_ms", c_int32),
-        ("grid_blocks", c_int32), ("poll_backoff_ns", c_int32), ("die_split", c_int32),
+        ("grid_blocks", c_int32), ("poll_backoff_ns", c_int32),
     ]
 
 
@@ -58,7 +58,7 @@ class Info(Structure):
         ("grid_blocks", c_int32), ("cta_run_rows", c_int32),
         ("thin_rows", c_int32), ("max_depth", c_int32), ("flop_budget", c_double),
         ("ir_iters_last", c_int32), ("num_sms", c_int32), ("poll_backoff_ns", c_int32),
-        ("chosen_depth", c_int32), ("die_split", c_int32),
+        ("chosen_depth", c_int32),
         ("analyze_ms", c_double), ("transform_ms", c_double),
     ]
 

@@ -415,20 +415,6 @@ sptrsv_status_t build_struct(sptrsv_plan_t p, SolveStruct<T> &ss, int L, cudaStr
                             ss.row_id.p, ss.diag.p, s));
     CK(ss.chunk_level.alloc(nchunks));
     CK(launch_chunk_level(nseg, ss.lvl_chunk.p, ss.chunk_level.p, s));
-    {   // die-aware schedule: first halves of every level, then second halves
-        std::vector<int32_t> seq0, seq1;
-        seq0.reserve(nchunks / 2 + nseg);
-        seq1.reserve(nchunks / 2 + nseg);
-        for (int32_t sg = 0; sg < nseg; ++sg) {
-            const int32_t c0 = lvl_chunk[sg], c1 = lvl_chunk[sg + 1];
-            const int32_t mid = c0 + (c1 - c0 + 1) / 2;
-            for (int32_t c = c0; c < mid; ++c) seq0.push_back(c);
-            for (int32_t c = mid; c < c1; ++c) seq1.push_back(c);
-        }
-        ss.dom_len0 = (int32_t)seq0.size();
-        seq0.insert(seq0.end(), seq1.begin(), seq1.end());
-        CK(upload(ss.dom_seq, seq0, s));
-    }
     CK(cudaStreamSynchronize(s));
     ss.n = p->n;
     ss.nlev = nseg;
@@ -577,7 +563,6 @@ sptrsv_status_t autotune(sptrsv_plan_t p, cudaStream_t s) {
             c.block_threads = bt_req > 0 ? bt_req : 512;
             c.grid = p->prm.grid_blocks > 0 ? p->prm.grid_blocks : (c.syncfree ? 0 : p->num_sms);
             c.backoff_ns = p->prm.poll_backoff_ns > 0 ? p->prm.poll_backoff_ns : 0;
-            c.die_split = p->prm.die_split > 0;
             c.cta_run_rows = mode == 1 ? c.block_threads / L : 0;
             if (p->prm.cta_run_rows < 0 && mode == 1) continue;
             p->cfg = c;
@@ -587,18 +572,6 @@ sptrsv_status_t autotune(sptrsv_plan_t p, cudaStream_t s) {
                 best_ms = ms;
                 best = c;
             }
-        }
-    }
-    // die-aware schedule of the synchronisation-free kernel
-    if (best.syncfree && p->prm.die_split < 0) {
-        SolveConfig c = best;
-        c.die_split = true;
-        p->cfg = c;
-        double ms;
-        CKS(time_cfg(&ms));
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = c;
         }
     }
     // polling back-off of the synchronisation-free kernel
@@ -672,10 +645,6 @@ sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t 
     if (p->prm.precision != SPTRSV_F32_IR) {
         SolveData<double> sd = p->s64.view();
         sd.backoff_ns = p->cfg.backoff_ns;
-        if (p->cfg.die_split && p->cfg.syncfree) {
-            sd.dom_len0 = p->s64.dom_len0;
-            sd.die_split_sm = p->num_sms / 2;
-        }
         if (p->cfg.syncfree) {
             // sentinel pre-fill first, so the events bracket the solve kernel alone
             for (int32_t c0 = 0; c0 < nrhs; c0 += 32)
@@ -702,10 +671,6 @@ sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t 
     CKS(ensure_ir(p, count));
     SolveData<float> sd = p->s32.view();
     sd.backoff_ns = p->cfg.backoff_ns;
-    if (p->cfg.die_split && p->cfg.syncfree) {
-        sd.dom_len0 = p->s32.dom_len0;
-        sd.die_split_sm = p->num_sms / 2;
-    }
     auto solve32 = [&](const double *rhs, bool skip) -> sptrsv_status_t {
         for (int32_t c0 = 0; c0 < nrhs; c0 += 32) {
             const int nr = std::min<int32_t>(32, nrhs - c0);
@@ -769,7 +734,6 @@ void sptrsv_default_params(sptrsv_transform_params_t *prm) {
     prm->wait_timeout_ms = 5000;
     prm->grid_blocks = 0;
     prm->poll_backoff_ns = -1;
-    prm->die_split = -1;
 }
 
 sptrsv_status_t sptrsv_analyze(int32_t n, int64_t nnz, const int32_t *d_row_ptr,
@@ -948,7 +912,6 @@ sptrsv_status_t sptrsv_transform(sptrsv_plan_t p, const sptrsv_transform_params_
     c.block_threads = p->prm.block_threads > 0 ? p->prm.block_threads : 512;
     c.grid = p->prm.grid_blocks > 0 ? p->prm.grid_blocks : (c.syncfree ? 0 : p->num_sms);
     c.backoff_ns = p->prm.poll_backoff_ns > 0 ? p->prm.poll_backoff_ns : 0;
-    c.die_split = p->prm.die_split > 0;
     c.L = 1;
     p->cfg = c;
     CKS(build_struct<double>(p, p->s64, 1, s));
@@ -1010,7 +973,6 @@ sptrsv_status_t sptrsv_get_info(sptrsv_plan_t p, sptrsv_info_t *o) {
     o->num_sms = p->num_sms;
     o->poll_backoff_ns = p->cfg.backoff_ns;
     o->chosen_depth = p->chosen_depth;
-    o->die_split = p->cfg.die_split && p->cfg.syncfree ? 1 : 0;
     o->analyze_ms = p->analyze_ms;
     o->transform_ms = p->transform_ms;
     if (p->status.p) {

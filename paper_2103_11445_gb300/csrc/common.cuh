@@ -30,7 +30,6 @@ struct DevStatus {
     unsigned long long exit_count;
     unsigned long long ir_flag;   // refinement converged flag
     double norms[4];              // scratch for infinity norms (as u64 bits)
-    int32_t die_cnt[2];           // CTAs registered per die (die-aware schedule)
 };
 
 __device__ __forceinline__ void latch_error(DevStatus *st, int code, int where) {
@@ -194,8 +193,6 @@ __device__ __forceinline__ void grid_exit(DevStatus *st) {
         if (prev == gridDim.x - 1) {
             atomicExch(&st->bar_count, 0ull);
             atomicExch(&st->exit_count, 0ull);
-            atomicExch(&st->die_cnt[0], 0);
-            atomicExch(&st->die_cnt[1], 0);
         }
     }
 }

@@ -55,8 +55,6 @@ struct SolveStruct {
     DevArr<int4> meta;
     DevArr<T> eval, diag;
     DevArr<int2> phases;
-    DevArr<int32_t> dom_seq;
-    int32_t dom_len0 = -1;
     int32_t n = 0, nlev = 0, nchunks = 0, L = 1, nphases = 0;
     int64_t nslots = 0;
     bool built = false;
@@ -75,9 +73,6 @@ struct SolveStruct {
         v.phases = phases.p;
         v.nphases = nphases;
         v.backoff_ns = 0;
-        v.dom_seq = dom_seq.p;
-        v.dom_len0 = -1;
-        v.die_split_sm = 0;
         return v;
     }
 };
@@ -89,7 +84,6 @@ struct SolveConfig {
     int grid = 0;
     int cta_run_rows = 0;   // resolved threshold (<= 0: no runs)
     int backoff_ns = 0;     // synchronisation-free polling back-off
-    bool die_split = false; // synchronisation-free: each die takes half of every level
 };
 
 }  // namespace sptrsv

@@ -470,40 +470,8 @@ solve_syncfree_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr
     // (Staging the next chunk's entries while this one waits measured slower
     // here than processing each chunk in turn: the staged loads compete with
     // the polls and pin registers; the barrier kernel keeps its staging.)
-    if (sd.dom_len0 < 0) {
-        for (int32_t c = gw; c < sd.nchunks; c += nw)
-            if (process_chunk<T, L, R, true>(sd, c, out, cx)) break;
-        return;
-    }
-    // Die-aware schedule: a hop between SMs of one die costs about half of a
-    // hop across dies, and rows of a level sorted by index depend mostly on
-    // the same half of the previous level.  CTAs register with the die of
-    // their SM; each die's warps walk that die's sequence (half of every
-    // level, in level order), so progress holds per die as it does for the
-    // whole grid.
-    __shared__ int32_t s_die, s_rank;
-    if (threadIdx.x == 0) {
-        unsigned smid;
-        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-        s_die = (int32_t)smid >= sd.die_split_sm ? 1 : 0;
-        s_rank = atomicAdd(&st->die_cnt[s_die], 1);
-    }
-    if (grid_barrier(st, gridDim.x, timeout_ns, -4)) {
-        const int32_t cnt0 = (int32_t)ld_relaxed_u32(&st->die_cnt[0]);
-        const int32_t cnt1 = (int32_t)ld_relaxed_u32(&st->die_cnt[1]);
-        if (cnt0 == 0 || cnt1 == 0) {  // one die holds every CTA: plain order
-            for (int32_t c = gw; c < sd.nchunks; c += nw)
-                if (process_chunk<T, L, R, true>(sd, c, out, cx)) break;
-        } else {
-            const int32_t die = s_die;
-            const int32_t wd = s_rank * wpb + (threadIdx.x >> 5);
-            const int32_t nwd = (die ? cnt1 : cnt0) * wpb;
-            const int32_t lo = die ? sd.dom_len0 : 0, hi = die ? sd.nchunks : sd.dom_len0;
-            for (int32_t k = lo + wd; k < hi; k += nwd)
-                if (process_chunk<T, L, R, true>(sd, __ldg(&sd.dom_seq[k]), out, cx)) break;
-        }
-    }
-    grid_exit(st);
+    for (int32_t c = gw; c < sd.nchunks; c += nw)
+        if (process_chunk<T, L, R, true>(sd, c, out, cx)) break;
 }
 
 template <typename T>

@@ -28,13 +28,6 @@ struct SolveData {
     const int2 *phases;         // barrier schedule: (l0, l1) level, or (l0, -l1) CTA-local run
     int32_t nphases;
     int32_t backoff_ns;         // sleep between failed polls (synchronisation-free), 0 = none
-    // die-aware schedule of the synchronisation-free kernel (dom_len0 < 0: off):
-    // dom_seq[0, dom_len0) = first half of every level's chunks, in level
-    // order, taken by CTAs on SMs [0, die_split_sm); dom_seq[dom_len0,
-    // nchunks) = second halves, taken by the other die's CTAs.
-    const int32_t *dom_seq;
-    int32_t dom_len0;
-    int32_t die_split_sm;
 };
 
 struct LaunchCfg {

@@ -71,8 +71,7 @@ def test_heuristic_matches_oracle(name, make, tau, d_max, rho):
     compare_rows(A, tr, t, range(A.n))
     assert info["flops_new"] - info["flops_plain"] == tr.added_flops
     b = mg.rhs_uniform(A.n, nrhs=2, seed=5)
-    for mode in (dict(solve_mode=1), dict(solve_mode=2, die_split=0),
-                 dict(solve_mode=2, die_split=1)):
+    for mode in (dict(solve_mode=1), dict(solve_mode=2)):
         P.transform(select_mode=1, thin_rows=min(tau, 2**31 - 1), max_depth=d_max,
                     flop_budget=budget, max_row_fill=1024, **mode)
         assert_close_to_oracle(A, gpu_solve(P, b), b, TOL64)
@@ -118,11 +117,11 @@ def test_fig2_example_on_device():
     assert t["bw"][b0] == -(l31 * l10) / (l11 * l00)
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3], ids=["barrier", "syncfree", "syncfree_dies"])
+@pytest.mark.parametrize("mode", [1, 2], ids=["barrier", "syncfree"])
 @pytest.mark.parametrize("d", [1, 3])
 def test_full_stencil3d_fixed_depth(mode, d):
     A = mg.stencil3d(128, seed=2000)
-    P = plan_for(A, select_mode=3, depth=d, solve_mode=min(mode, 2), die_split=int(mode == 3))
+    P = plan_for(A, select_mode=3, depth=d, solve_mode=mode)
     info = P.info()
     assert info["nlev_new"] == -(-382 // (d + 1))
     b = mg.rhs_uniform(A.n, seed=2001)
