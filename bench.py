@@ -430,7 +430,7 @@ def run_ours(args, world, rank, local):
             e2e_ms.append(e0.elapsed_time(e1))
     P.check()
     e2e_val = B * world / (max_over_ranks(world, statistics.mean(e2e_ms)) * 1e-3) / 1e9
-    launches_per_solve = 2 if info["solve_mode"] == Bd.SOLVE_SYNCFREE else 1
+    launches_per_solve = 1
 
     line = {
         "metric": "SpTRSV eff. GB/s (B_alg / t_solve), rewritten + autotuned, FP64",
@@ -440,7 +440,8 @@ def run_ours(args, world, rank, local):
         "config": {
             "workload": workload_name(args, A),
             "b_alg_bytes": B, "levels": nlev, "levels_after": info["nlev_new"],
-            "selection": best, "solve_mode": "syncfree" if launches_per_solve == 2 else "barrier",
+            "selection": best,
+            "solve_mode": "syncfree" if info["solve_mode"] == Bd.SOLVE_SYNCFREE else "barrier",
             "lanes_per_row": info["lanes_per_row"], "block_threads": info["block_threads"],
             "grid_blocks": info["grid_blocks"], "cta_run_rows": info["cta_run_rows"],
             "flops_plain": info["flops_plain"], "flops_rewritten": info["flops_new"],

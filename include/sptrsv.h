@@ -302,8 +302,8 @@ SPTRSV_API sptrsv_status_t sptrsv_solve_ir_noalloc(sptrsv_plan_t p, const double
                                                    sptrsv_stream_t stream);
 
 /* Profiling (not part of the paper's method): while enabled, sptrsv_solve
- * records CUDA events on its stream around its main solve kernel(s) (after
- * the sentinel pre-fill of the synchronisation-free variant; FP64 only).
+ * records CUDA events on its stream around its solve kernel launch(es)
+ * (FP64 only).
  * sptrsv_last_kernel_ms waits for the last solve's end event and returns the
  * elapsed milliseconds; SPTRSV_ERR_BAD_STATE if no profiled solve ran. */
 SPTRSV_API sptrsv_status_t sptrsv_set_profiling(sptrsv_plan_t p, int32_t on);

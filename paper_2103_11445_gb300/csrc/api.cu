@@ -419,6 +419,8 @@ sptrsv_status_t build_struct(sptrsv_plan_t p, SolveStruct<T> &ss, int L, cudaStr
     ss.n = p->n;
     ss.nlev = nseg;
     ss.nchunks = nchunks;
+    ss.run_encoded = -1;
+    ss.run_slots = 0;
     ss.L = L;
     ss.nslots = total;
     ss.built = true;
@@ -426,7 +428,12 @@ sptrsv_status_t build_struct(sptrsv_plan_t p, SolveStruct<T> &ss, int L, cudaStr
 }
 
 // Phases of the barrier kernel: maximal runs (>= 2) of consecutive levels of
-// at most run_rows rows become one CTA-local phase.
+// at most run_rows rows become one CTA-local phase, each holding at most
+// kMaxRunSlots rows in total (its unknowns live in shared memory); the run
+// chunks' x terms that read rows of the same run are then encoded as
+// shared-memory slots.
+constexpr int32_t kMaxRunSlots = 8192;
+
 template <typename T>
 sptrsv_status_t build_phases(sptrsv_plan_t p, SolveStruct<T> &ss, int run_rows, cudaStream_t s) {
     std::vector<int2> ph;
@@ -442,7 +449,12 @@ sptrsv_status_t build_phases(sptrsv_plan_t p, SolveStruct<T> &ss, int run_rows, 
             // barrier never wait longer than a fraction of the wait bound
             constexpr int32_t kMaxRunLevels = 16384;
             int32_t e = sg;
-            while (e < nseg && e - sg < kMaxRunLevels && seg_rows(e) <= run_rows) ++e;
+            int64_t rows = 0;
+            while (e < nseg && e - sg < kMaxRunLevels && seg_rows(e) <= run_rows &&
+                   rows + seg_rows(e) <= kMaxRunSlots) {
+                rows += seg_rows(e);
+                ++e;
+            }
             if (e - sg >= 2) {
                 ph.push_back(make_int2(sg, -e));
                 sg = e;
@@ -453,8 +465,43 @@ sptrsv_status_t build_phases(sptrsv_plan_t p, SolveStruct<T> &ss, int run_rows, 
         ++sg;
     }
     CK(upload(ss.phases, ph, s));
-    CK(cudaStreamSynchronize(s));
     ss.nphases = (int32_t)ph.size();
+    // shared-memory slots for the unknowns of each run
+    std::vector<int32_t> run_chunk;
+    std::vector<int2> run_span;
+    std::vector<int32_t> lvl_chunk(nseg + 1);
+    CK(cudaMemcpy(lvl_chunk.data(), ss.lvl_chunk.p, (nseg + 1) * sizeof(int32_t),
+                  cudaMemcpyDeviceToHost));
+    int32_t slots = 0;
+    for (const int2 &q : ph) {
+        if (q.y > 0) continue;
+        const int32_t l0 = q.x, l1 = -q.y;
+        const int32_t P0 = p->h_level_ptr[p->seg_first[l0]];
+        const int32_t P1 = p->h_level_ptr[p->seg_first[l1 - 1] + p->seg_depth[l1 - 1] + 1];
+        slots = std::max(slots, P1 - P0);
+        for (int32_t c = lvl_chunk[l0]; c < lvl_chunk[l1]; ++c) {
+            run_chunk.push_back(c);
+            run_span.push_back(make_int2(P0, P1));
+        }
+    }
+    ss.run_slots = slots;
+    {
+        std::vector<int32_t> p0(ss.nchunks, -1);
+        for (size_t i = 0; i < run_chunk.size(); ++i) p0[run_chunk[i]] = run_span[i].x;
+        CK(upload(ss.chunk_run_p0, p0, s));
+    }
+    if (!run_chunk.empty()) {
+        DevArr<int32_t> d_rc, pos;
+        DevArr<int2> d_rs;
+        CK(upload(d_rc, run_chunk, s));
+        CK(upload(d_rs, run_span, s));
+        CK(pos.alloc(p->n));
+        CK(launch_encode_runs(p->n, ss.L, ss.row_id.p, ss.meta.p, (int32_t)run_chunk.size(),
+                              d_rc.p, d_rs.p, pos.p, ss.ecol.p, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    CK(cudaStreamSynchronize(s));
+    ss.run_encoded = run_rows;
     return SPTRSV_OK;
 }
 
@@ -472,8 +519,11 @@ int auto_lanes(sptrsv_plan_t p) {
 
 int grid_for(sptrsv_plan_t p, int nr, bool f32) {
     const SolveConfig &c = p->cfg;
-    const int mx = f32 ? max_coresident_ctas<float>(c.L, nr, c.syncfree, c.block_threads, p->num_sms)
-                       : max_coresident_ctas<double>(c.L, nr, c.syncfree, c.block_threads, p->num_sms);
+    const int mx =
+        f32 ? max_coresident_ctas<float>(c.L, nr, c.syncfree, c.block_threads, p->num_sms,
+                                         p->s32.run_slots)
+            : max_coresident_ctas<double>(c.L, nr, c.syncfree, c.block_threads, p->num_sms,
+                                          p->s64.run_slots);
     if (mx <= 0) return 0;
     int g = c.grid > 0 ? c.grid : mx;
     return std::min(g, mx);
@@ -493,7 +543,7 @@ sptrsv_status_t count_terms(sptrsv_plan_t p, cudaStream_t s) {
     CK(bs.alloc(n + 1));
     CK(tmp.alloc(scan_tmp_elems(n)));
     CK(launch_export_count(p->s64.nchunks, p->s64.L, p->s64.meta.p, p->s64.ecol.p,
-                           p->s64.row_id.p, xc.p, bc.p, s));
+                           p->s64.row_id.p, p->n, xc.p, bc.p, s));
     CK(exclusive_scan_i64_i64(xc.p, xs.p, n, tmp.p, s));
     CK(exclusive_scan_i64_i64(bc.p, bs.p, n, tmp.p, s));
     CK(cudaMemcpyAsync(&p->nnz_x, xs.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -504,12 +554,18 @@ sptrsv_status_t count_terms(sptrsv_plan_t p, cudaStream_t s) {
 
 sptrsv_status_t apply_config(sptrsv_plan_t p, cudaStream_t s) {
     const bool f32 = p->prm.precision == SPTRSV_F32_IR;
-    if (p->s64.L != p->cfg.L || !p->s64.built) CKS(build_struct<double>(p, p->s64, p->cfg.L, s));
-    CKS(build_phases<double>(p, p->s64, p->cfg.cta_run_rows, s));
+    // run slots are encoded into the entries: a new run threshold needs a
+    // freshly assembled structure
+    const int runs = p->cfg.syncfree ? 0 : p->cfg.cta_run_rows;
+    if (p->s64.L != p->cfg.L || !p->s64.built ||
+        (p->s64.run_encoded > 0 && p->s64.run_encoded != runs))
+        CKS(build_struct<double>(p, p->s64, p->cfg.L, s));
+    if (p->s64.run_encoded != runs) CKS(build_phases<double>(p, p->s64, runs, s));
     if (f32) {
-        if (p->s32.L != p->cfg.L || !p->s32.built)
+        if (p->s32.L != p->cfg.L || !p->s32.built ||
+            (p->s32.run_encoded > 0 && p->s32.run_encoded != runs))
             CKS(build_struct<float>(p, p->s32, p->cfg.L, s));
-        CKS(build_phases<float>(p, p->s32, p->cfg.cta_run_rows, s));
+        if (p->s32.run_encoded != runs) CKS(build_phases<float>(p, p->s32, runs, s));
     }
     return SPTRSV_OK;
 }
@@ -645,12 +701,6 @@ sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t 
     if (p->prm.precision != SPTRSV_F32_IR) {
         SolveData<double> sd = p->s64.view();
         sd.backoff_ns = p->cfg.backoff_ns;
-        if (p->cfg.syncfree) {
-            // sentinel pre-fill first, so the events bracket the solve kernel alone
-            for (int32_t c0 = 0; c0 < nrhs; c0 += 32)
-                CK(launch_fill_sentinel<double>(x + c0, n, nrhs, std::min<int32_t>(32, nrhs - c0),
-                                                p->status.p, false, s));
-        }
         if (p->profiling) CK(cudaEventRecord(p->prof_ev[0], s));
         for (int32_t c0 = 0; c0 < nrhs; c0 += 32) {
             const int nr = std::min<int32_t>(32, nrhs - c0);
@@ -1033,7 +1083,7 @@ sptrsv_status_t sptrsv_get_transformed(sptrsv_plan_t p, int32_t *d_new_level, in
     CK(bc.alloc(n));
     CK(tmp.alloc(scan_tmp_elems(n)));
     CK(launch_export_count(p->s64.nchunks, p->s64.L, p->s64.meta.p, p->s64.ecol.p,
-                           p->s64.row_id.p, xc.p, bc.p, s));
+                           p->s64.row_id.p, p->n, xc.p, bc.p, s));
     int64_t *xptr = d_xptr, *bptr = d_bptr;
     if (!xptr) {
         CK(xp.alloc(n + 1));
@@ -1046,8 +1096,8 @@ sptrsv_status_t sptrsv_get_transformed(sptrsv_plan_t p, int32_t *d_new_level, in
     CK(exclusive_scan_i64_i64(xc.p, xptr, n, tmp.p, s));
     CK(exclusive_scan_i64_i64(bc.p, bptr, n, tmp.p, s));
     CK(launch_export_fill(p->s64.nchunks, p->s64.L, p->s64.meta.p, p->s64.ecol.p, p->s64.eval.p,
-                          p->s64.row_id.p, p->s64.chunk_level.p, xptr, bptr, d_xcol, d_xval,
-                          d_bcol, d_bw, d_new_level, s));
+                          p->s64.row_id.p, p->s64.chunk_level.p, p->s64.chunk_run_p0.p, p->n,
+                          xptr, bptr, d_xcol, d_xval, d_bcol, d_bw, d_new_level, s));
     CK(cudaStreamSynchronize(s));
     return SPTRSV_OK;
 }

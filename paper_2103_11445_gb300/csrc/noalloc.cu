@@ -90,7 +90,7 @@ extern "C" SPTRSV_API sptrsv_status_t sptrsv_solve_ir_noalloc(sptrsv_plan_t p, c
         for (int32_t c0 = 0; c0 < nrhs; c0 += 32) {
             const int nr = nrhs - c0 < 32 ? nrhs - c0 : 32;
             const int mx = max_coresident_ctas<float>(c.L, nr, c.syncfree, c.block_threads,
-                                                      p->num_sms);
+                                                      p->num_sms, p->s32.run_slots);
             if (mx <= 0) return cudaErrorInvalidConfiguration;
             LaunchCfg lc{c.block_threads, c.grid > 0 && c.grid < mx ? c.grid : mx};
             cudaError_t le = launch_solve<float>(sd, rhs + c0, d32 + c0, n, nrhs, nr, c.syncfree,

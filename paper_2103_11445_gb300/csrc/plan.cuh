@@ -56,6 +56,9 @@ struct SolveStruct {
     DevArr<T> eval, diag;
     DevArr<int2> phases;
     int32_t n = 0, nlev = 0, nchunks = 0, L = 1, nphases = 0;
+    int32_t run_slots = 0;      // rows of the largest CTA-local run (shared memory)
+    DevArr<int32_t> chunk_run_p0;  // first position of the chunk's run, -1 outside runs
+    int32_t run_encoded = -1;   // run threshold the entries are encoded for (-1: none)
     int64_t nslots = 0;
     bool built = false;
     SolveData<T> view() const {
@@ -73,6 +76,7 @@ struct SolveStruct {
         v.phases = phases.p;
         v.nphases = nphases;
         v.backoff_ns = 0;
+        v.run_slots = run_slots;
         return v;
     }
 };

@@ -137,10 +137,32 @@ struct Ctx {
     uint64_t timeout_ns;
     int backoff_ns;
     bool rhs_coherent;   // rhs was written earlier in this launch: read it through L2
+    int32_t n;           // rows (decodes b terms and run slots)
+    const int32_t *row_id;
+    void *xs;            // shared-memory unknowns of the current CTA-local run, or null
+    int32_t run_p0;      // first solve position of the current run
 };
 
 __device__ __forceinline__ double load_rhs(const Ctx &cx, int64_t i) {
     return cx.rhs_coherent ? __ldcg(cx.rhs + i) : __ldg(cx.rhs + i);
+}
+
+// A term that is not an unknown of another CTA: a b term of a rewritten row
+// (col = ~j), a padding slot, or -- inside a CTA-local run -- an unknown of
+// the same run (col = -(n + 1) - slot, kept in shared memory; the
+// several-right-hand-side path reads it back from x through L2).
+template <typename T>
+__device__ __forceinline__ T other_term(const Ctx &cx, int32_t c, const T *out, int r) {
+    if (c >= -cx.n) return (T)load_rhs(cx, (int64_t)(~c) * cx.ld + r);
+    if (c == PAD_COL) return T(0);
+    const int32_t slot = -(cx.n + 1) - c;
+    if (cx.xs) return reinterpret_cast<const T *>(cx.xs)[slot];
+    return __ldcg(out + (int64_t)__ldg(&cx.row_id[cx.run_p0 + slot]) * cx.ld + r);
+}
+
+template <typename T>
+__device__ __forceinline__ void keep_in_run(const Ctx &cx, int32_t pos, T v) {
+    if (cx.xs) reinterpret_cast<T *>(cx.xs)[pos - cx.run_p0] = v;
 }
 
 // One right-hand side; L lanes per row (compile time).
@@ -177,8 +199,7 @@ __device__ __forceinline__ bool chunk_one(const SolveData<T> &sd, int32_t c, T *
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (cc[u] >= 0) xv[u] = load_x<T, SF>(out + (int64_t)cc[u] * cx.ld);
-                else if (cc[u] != PAD_COL) xv[u] = (T)load_rhs(cx, (int64_t)(~cc[u]) * cx.ld);
-                else xv[u] = T(0);
+                else xv[u] = other_term<T>(cx, cc[u], out, 0);
             }
             T pr[U];
 #pragma unroll
@@ -198,15 +219,19 @@ __device__ __forceinline__ bool chunk_one(const SolveData<T> &sd, int32_t c, T *
                 xv = load_x<T, SF>(out + (int64_t)cc * cx.ld);
                 if (SF && Bits<T>::of(xv) == Sentinel<T>::bits)
                     xv = wait_x<T>(out + (int64_t)cc * cx.ld, cx.st, cx.timeout_ns, bail);
-            } else if (cc != PAD_COL) {
-                xv = (T)load_rhs(cx, (int64_t)(~cc) * cx.ld);
+            } else {
+                xv = other_term<T>(cx, cc, out, 0);
             }
             acc = fma(v, xv, acc);
         }
     }
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
-    if (active && s == 0) store_x<T, SF>(out + (int64_t)r * cx.ld, div_by_diag<T>(brow - acc, dg, dy));
+    if (active && s == 0) {
+        const T res = div_by_diag<T>(brow - acc, dg, dy);
+        store_x<T, SF>(out + (int64_t)r * cx.ld, res);
+        keep_in_run<T>(cx, mt.x + k, res);
+    }
     return __any_sync(FULL_MASK, bail);
 }
 
@@ -248,7 +273,7 @@ __device__ __forceinline__ bool chunk_multi(const SolveData<T> &sd, int32_t c, T
                         if (SF && Bits<T>::of(xv) == Sentinel<T>::bits)
                             xv = wait_x<T>(px, cx.st, cx.timeout_ns, bail);
                     } else {
-                        xv = (T)load_rhs(cx, (int64_t)(~cc) * cx.ld + r);
+                        xv = other_term<T>(cx, cc, out, r);
                     }
                     acc = fma(v, xv, acc);
                 }
@@ -323,8 +348,7 @@ __device__ __forceinline__ bool finish_staged(const SolveData<T> &sd, const Stag
     for (int u = 0; u < kPipeSteps; ++u) {
         const int32_t c = sg.col[u];
         if (c >= 0) xv[u] = load_x<T, SF>(out + (int64_t)c * cx.ld);
-        else if (c != PAD_COL) xv[u] = (T)load_rhs(cx, (int64_t)(~c) * cx.ld);
-        else xv[u] = T(0);
+        else xv[u] = other_term<T>(cx, c, out, 0);
     }
     bool bail = false;
     T pr[kPipeSteps];
@@ -339,8 +363,11 @@ __device__ __forceinline__ bool finish_staged(const SolveData<T> &sd, const Stag
     T acc = (pr[0] + pr[1]) + (pr[2] + pr[3]);
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
-    if (active && s == 0)
-        store_x<T, SF>(out + (int64_t)sg.row * cx.ld, div_by_diag<T>(brow - acc, sg.diag, sg.rdiag));
+    if (active && s == 0) {
+        const T res = div_by_diag<T>(brow - acc, sg.diag, sg.rdiag);
+        store_x<T, SF>(out + (int64_t)sg.row * cx.ld, res);
+        keep_in_run<T>(cx, sg.mt.x + k, res);
+    }
     return __any_sync(FULL_MASK, bail);
 }
 
@@ -406,7 +433,8 @@ __global__ void __launch_bounds__(kMaxSolveThreads)
 solve_barrier_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr,
                      DevStatus *st, uint64_t timeout_ns, int skip_if_converged) {
     if (skip_if_converged && converged(st)) return;  // uniform: set by an earlier kernel
-    const Ctx cx{rhs, ld, nr, st, timeout_ns, 0, false};
+    extern __shared__ __align__(16) unsigned char run_smem[];
+    const Ctx cx{rhs, ld, nr, st, timeout_ns, 0, false, sd.n, sd.row_id, nullptr, 0};
     const int wpb = blockDim.x >> 5, wib = threadIdx.x >> 5;
     const int32_t gw = blockIdx.x * wpb + wib;
     const int32_t nw = gridDim.x * wpb;
@@ -429,11 +457,16 @@ solve_barrier_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr,
                 else process_chunk<T, L, R, false>(sd, c, out, cx);
             }
         } else if ((int)blockIdx.x == ph % (int)gridDim.x) {
+            // CTA-local run: its unknowns also go to shared memory, where the
+            // run's later levels read them
+            Ctx rc = cx;
+            rc.run_p0 = __ldg(&sd.meta[__ldg(&sd.lvl_chunk[p.x])]).x;
+            rc.xs = (R == 1 && sd.run_slots > 0) ? (void *)run_smem : nullptr;
             for (int32_t l = p.x; l < -p.y; ++l) {
                 const int32_t c1 = __ldg(&sd.lvl_chunk[l + 1]);
                 for (int32_t c = __ldg(&sd.lvl_chunk[l]) + wib; c < c1; c += wpb) {
-                    if (R == 1 && c == staged) finish_any<T, L, false>(sd, c, sg, out, cx);
-                    else process_chunk<T, L, R, false>(sd, c, out, cx);
+                    if (R == 1 && c == staged) finish_any<T, L, false>(sd, c, sg, out, rc);
+                    else process_chunk<T, L, R, false>(sd, c, out, rc);
                 }
                 if (R == 1 && l + 1 < -p.y) {
                     const int32_t c = __ldg(&sd.lvl_chunk[l + 1]) + wib;
@@ -458,11 +491,25 @@ __global__ void __launch_bounds__(kMaxSolveThreads)
 solve_syncfree_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr,
                       DevStatus *st, uint64_t timeout_ns, int skip_if_converged) {
     if (skip_if_converged && converged(st)) return;
-    const Ctx cx{rhs, ld, nr, st, timeout_ns, sd.backoff_ns, false};
+    const Ctx cx{rhs, ld, nr, st, timeout_ns, sd.backoff_ns, false, sd.n, sd.row_id, nullptr, 0};
     const int wpb = blockDim.x >> 5;
     const int32_t gw = blockIdx.x * wpb + (threadIdx.x >> 5);
     const int32_t nw = gridDim.x * wpb;
     prefetch_solve_inputs<T>(sd, rhs, sd.n, ld, nr);
+    // every unknown of this launch starts as the "not computed" sentinel; one
+    // grid barrier orders those stores before any poll
+    {
+        const int64_t total = (int64_t)sd.n * nr;
+        const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gthreads) {
+            const int64_t row = i / nr, col = i % nr;
+            *reinterpret_cast<typename Bits<T>::U *>(out + row * ld + col) = Sentinel<T>::bits;
+        }
+    }
+    if (!grid_barrier(st, gridDim.x, timeout_ns, -5)) {
+        grid_exit(st);
+        return;
+    }
     // Chunks are taken in level order, each warp its own arithmetic sequence:
     // with every warp resident, the lowest unfinished chunk's warp has
     // finished its earlier chunks and all that chunk's dependencies lie in
@@ -472,6 +519,7 @@ solve_syncfree_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr
     // the polls and pin registers; the barrier kernel keeps its staging.)
     for (int32_t c = gw; c < sd.nchunks; c += nw)
         if (process_chunk<T, L, R, true>(sd, c, out, cx)) break;
+    grid_exit(st);
 }
 
 template <typename T>
@@ -628,7 +676,7 @@ __device__ __forceinline__ bool batch_solve_group(const SolveData<T> &sd, const 
                                                   bool rhs_coherent, T *out, int nr, int R,
                                                   DevStatus *st, uint64_t timeout_ns, int32_t gw,
                                                   int32_t nw) {
-    const Ctx cx{rhs, nr, nr, st, timeout_ns, 0, rhs_coherent};
+    const Ctx cx{rhs, nr, nr, st, timeout_ns, 0, rhs_coherent, sd.n, sd.row_id, nullptr, 0};
     for (int32_t c = gw; c < sd.nchunks; c += nw)
         if (batch_chunk<T>(sd, c, out, cx, R)) return false;
     return true;
@@ -755,17 +803,28 @@ cudaError_t launch_batch(const BatchMat *mats, int32_t nmats, BatchCtl *ctl, Dev
 }
 
 template <typename T>
-int max_coresident_ctas(int L, int nr, bool syncfree, int block_threads, int num_sms) {
+size_t run_smem_bytes(int nr, bool syncfree, int run_slots) {
+    return (!syncfree && nr <= 1 && run_slots > 0) ? (size_t)run_slots * sizeof(T) : 0;
+}
+
+template <typename T>
+int max_coresident_ctas(int L, int nr, bool syncfree, int block_threads, int num_sms,
+                        int run_slots) {
     const void *k = pick_kernel<T>(L, nr, syncfree);
     if (!k) return 0;
+    const size_t smem = run_smem_bytes<T>(nr, syncfree, run_slots);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+        return 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block_threads, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block_threads, smem) !=
         cudaSuccess)
         return 0;
     return per_sm * num_sms;
 }
-template int max_coresident_ctas<double>(int, int, bool, int, int);
-template int max_coresident_ctas<float>(int, int, bool, int, int);
+template int max_coresident_ctas<double>(int, int, bool, int, int, int);
+template int max_coresident_ctas<float>(int, int, bool, int, int, int);
 
 template <typename T>
 cudaError_t launch_fill_sentinel(T *out, int32_t n, int ld, int nr, DevStatus *st,
@@ -790,10 +849,7 @@ cudaError_t launch_solve(const SolveData<T> &sd, const double *rhs, T *out, int3
     const void *k = pick_kernel<T>(sd.L, nr, syncfree);
     if (!k) return cudaErrorInvalidValue;
     const int skip = skip_if_converged ? 1 : 0;
-    if (syncfree && !prefilled) {
-        cudaError_t e = launch_fill_sentinel<T>(out, n, ld, nr, st, skip_if_converged, s);
-        if (e != cudaSuccess) return e;
-    }
+    (void)prefilled;  // the synchronisation-free kernel fills its own sentinels
     SolveData<T> sdc = sd;
     void *args[] = {(void *)&sdc, (void *)&rhs,        (void *)&out,  (void *)&ld,
                     (void *)&nr,  (void *)&st,         (void *)&timeout_ns,
@@ -801,7 +857,12 @@ cudaError_t launch_solve(const SolveData<T> &sd, const double *rhs, T *out, int3
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(cfg.grid);
     lc.blockDim = dim3(cfg.block_threads);
-    lc.dynamicSmemBytes = 0;
+    lc.dynamicSmemBytes = run_smem_bytes<T>(nr, syncfree, sd.run_slots);
+    if (lc.dynamicSmemBytes > 48 * 1024) {
+        cudaError_t ea = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)lc.dynamicSmemBytes);
+        if (ea != cudaSuccess) return ea;
+    }
     lc.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;

@@ -28,6 +28,11 @@ struct SolveData {
     const int2 *phases;         // barrier schedule: (l0, l1) level, or (l0, -l1) CTA-local run
     int32_t nphases;
     int32_t backoff_ns;         // sleep between failed polls (synchronisation-free), 0 = none
+    // CTA-local runs keep the unknowns they produce in shared memory: entries
+    // of run chunks that read a row of the same run are encoded as
+    // col = -(n + 1) - slot, slot = solve position - first position of the
+    // run; run_slots = largest run (rows), 0 when there are no runs.
+    int32_t run_slots;
 };
 
 struct LaunchCfg {
@@ -37,8 +42,8 @@ struct LaunchCfg {
 
 // x = L^{-1} rhs for `nr` right-hand sides stored with leading dimension ld
 // (row i, column r at [i * ld + r]).  rhs is FP64; out has type T.
-// syncfree selects the synchronisation-free kernel (out is pre-filled with
-// the sentinel by this launcher).  `skip_if_converged`: the kernels return
+// syncfree selects the synchronisation-free kernel (it pre-fills out with
+// the "not computed" sentinel itself, then one grid barrier).  `skip_if_converged`: the kernels return
 // at once when st->ir_flag is set (refinement loop).
 template <typename T>
 cudaError_t launch_solve(const SolveData<T> &sd, const double *rhs, T *out, int32_t n,
@@ -50,9 +55,11 @@ template <typename T>
 cudaError_t launch_fill_sentinel(T *out, int32_t n, int ld, int nr, DevStatus *st,
                                  bool skip_if_converged, cudaStream_t s);
 
-// Largest co-resident grid for the chosen kernel (CTAs per SM * SMs).
+// Largest co-resident grid for the chosen kernel (CTAs per SM * SMs), with
+// the dynamic shared memory the barrier kernel's runs need.
 template <typename T>
-int max_coresident_ctas(int L, int nr, bool syncfree, int block_threads, int num_sms);
+int max_coresident_ctas(int L, int nr, bool syncfree, int block_threads, int num_sms,
+                        int run_slots = 0);
 
 // ---------------------------------------------------------------------------
 // Batched solve: many independent plans in one persistent launch.  Matrix m

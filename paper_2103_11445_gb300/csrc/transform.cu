@@ -357,10 +357,11 @@ __global__ void chunk_fill_kernel(int32_t nchunks, int H, int L,
     }
 }
 
-// Export (tests): per original row, counts of x and b terms
+// Export (tests): per original row, counts of x and b terms.  Columns
+// < -n (not PAD) are run slots of a CTA-local run: x terms.
 __global__ void export_count_kernel(int32_t nchunks, int H, int L, const int4 *__restrict__ meta,
                                     const int32_t *__restrict__ ecol,
-                                    const int32_t *__restrict__ row_id,
+                                    const int32_t *__restrict__ row_id, int32_t n,
                                     int64_t *xcnt, int64_t *bcnt) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t c = g / H;
@@ -372,7 +373,8 @@ __global__ void export_count_kernel(int32_t nchunks, int H, int L, const int4 *_
     int64_t nx = 0, nb = 0;
     for (int32_t j = 0; j < mt.z * L; ++j) {
         const int32_t cc = ecol[mt.w + (int64_t)(j / L) * stride + (int64_t)k * L + (j % L)];
-        if (cc >= 0) ++nx; else if (cc != PAD_COL) ++nb;
+        if (cc == PAD_COL) continue;
+        if (cc >= 0 || cc < -n) ++nx; else ++nb;
     }
     const int32_t r = row_id[mt.x + k];
     xcnt[r] = nx;
@@ -384,6 +386,7 @@ __global__ void export_fill_kernel(int32_t nchunks, int H, int L, const int4 *__
                                    const int32_t *__restrict__ ecol, const T *__restrict__ eval,
                                    const int32_t *__restrict__ row_id,
                                    const int32_t *__restrict__ chunk_level,
+                                   const int32_t *__restrict__ chunk_run_p0, int32_t n,
                                    const int64_t *__restrict__ xptr,
                                    const int64_t *__restrict__ bptr, int32_t *xcol,
                                    double *xval, int32_t *bcol, double *bw,
@@ -399,12 +402,14 @@ __global__ void export_fill_kernel(int32_t nchunks, int H, int L, const int4 *__
     int64_t px = xptr ? xptr[r] : 0, pb = bptr ? bptr[r] : 0;
     for (int32_t j = 0; j < mt.z * L; ++j) {
         const int64_t slot = mt.w + (int64_t)(j / L) * stride + (int64_t)k * L + (j % L);
-        const int32_t cc = ecol[slot];
+        int32_t cc = ecol[slot];
+        if (cc == PAD_COL) continue;
+        if (cc < -n) cc = row_id[chunk_run_p0[c] + (-(n + 1) - cc)];  // run slot -> row
         if (cc >= 0) {
             if (xcol) xcol[px] = cc;
             if (xval) xval[px] = (double)eval[slot];
             ++px;
-        } else if (cc != PAD_COL) {
+        } else {
             if (bcol) bcol[pb] = ~cc;
             if (bw) bw[pb] = (double)eval[slot];
             ++pb;
@@ -419,6 +424,35 @@ __global__ void chunk_level_kernel(int32_t nlev, const int32_t *__restrict__ lvl
     if (l >= nlev) return;
     for (int32_t c = lvl_chunk[l] + threadIdx.x; c < lvl_chunk[l + 1]; c += blockDim.x)
         chunk_level[c] = l;
+}
+
+__global__ void pos_of_row_kernel(int32_t n, const int32_t *__restrict__ row_id,
+                                  int32_t *__restrict__ pos) {
+    const int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) pos[row_id[p]] = p;
+}
+
+// Run chunks: an x term whose row lies in the same run [P0, P1) of solve
+// positions becomes the shared-memory slot -(n + 1) - (pos - P0).
+__global__ void encode_run_kernel(int32_t nrc, const int32_t *__restrict__ run_chunk,
+                                  const int2 *__restrict__ run_span, int H, int L, int32_t n,
+                                  const int4 *__restrict__ meta, const int32_t *__restrict__ pos,
+                                  int32_t *__restrict__ ecol) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = g / H;
+    const int k = (int)(g % H);
+    if (i >= nrc) return;
+    const int4 mt = meta[run_chunk[i]];
+    if (k >= mt.y) return;
+    const int2 span = run_span[i];
+    const int64_t stride = (int64_t)mt.y * L;
+    for (int32_t j = 0; j < mt.z * L; ++j) {
+        const int64_t slot = mt.w + (int64_t)(j / L) * stride + (int64_t)k * L + (j % L);
+        const int32_t c = ecol[slot];
+        if (c < 0) continue;
+        const int32_t q = pos[c];
+        if (q >= span.x && q < span.y) ecol[slot] = -(n + 1) - (q - span.x);
+    }
 }
 
 __global__ void f64_to_f32(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
@@ -543,27 +577,28 @@ template cudaError_t launch_chunk_fill<float>(int32_t, int, const int32_t *, con
                                               cudaStream_t);
 
 cudaError_t launch_export_count(int32_t nchunks, int L, const int4 *meta, const int32_t *ecol,
-                                const int32_t *row_id, int64_t *xcnt, int64_t *bcnt,
+                                const int32_t *row_id, int32_t n, int64_t *xcnt, int64_t *bcnt,
                                 cudaStream_t s) {
     if (nchunks == 0) return cudaSuccess;
     const int H = 32 / L;
     const int64_t threads = (int64_t)nchunks * H;
     export_count_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-        nchunks, H, L, meta, ecol, row_id, xcnt, bcnt);
+        nchunks, H, L, meta, ecol, row_id, n, xcnt, bcnt);
     return cudaGetLastError();
 }
 
 cudaError_t launch_export_fill(int32_t nchunks, int L, const int4 *meta, const int32_t *ecol,
                                const double *eval, const int32_t *row_id,
-                               const int32_t *chunk_level, const int64_t *xptr,
-                               const int64_t *bptr, int32_t *xcol, double *xval,
-                               int32_t *bcol, double *bw, int32_t *new_level, cudaStream_t s) {
+                               const int32_t *chunk_level, const int32_t *chunk_run_p0,
+                               int32_t n, const int64_t *xptr, const int64_t *bptr,
+                               int32_t *xcol, double *xval, int32_t *bcol, double *bw,
+                               int32_t *new_level, cudaStream_t s) {
     if (nchunks == 0) return cudaSuccess;
     const int H = 32 / L;
     const int64_t threads = (int64_t)nchunks * H;
     export_fill_kernel<double><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-        nchunks, H, L, meta, ecol, eval, row_id, chunk_level, xptr, bptr, xcol, xval, bcol, bw,
-        new_level);
+        nchunks, H, L, meta, ecol, eval, row_id, chunk_level, chunk_run_p0, n, xptr, bptr, xcol,
+        xval, bcol, bw, new_level);
     return cudaGetLastError();
 }
 
@@ -571,6 +606,18 @@ cudaError_t launch_chunk_level(int32_t nlev, const int32_t *lvl_chunk, int32_t *
                                cudaStream_t s) {
     if (nlev == 0) return cudaSuccess;
     chunk_level_kernel<<<nlev, 128, 0, s>>>(nlev, lvl_chunk, chunk_level);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encode_runs(int32_t n, int L, const int32_t *row_id, const int4 *meta,
+                               int32_t nrc, const int32_t *run_chunk, const int2 *run_span,
+                               int32_t *pos_tmp, int32_t *ecol, cudaStream_t s) {
+    if (n == 0 || nrc == 0) return cudaSuccess;
+    pos_of_row_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, row_id, pos_tmp);
+    const int H = 32 / L;
+    const int64_t threads = (int64_t)nrc * H;
+    encode_run_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(nrc, run_chunk, run_span, H,
+                                                                       L, n, meta, pos_tmp, ecol);
     return cudaGetLastError();
 }
 

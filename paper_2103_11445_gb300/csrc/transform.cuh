@@ -35,16 +35,24 @@ cudaError_t launch_chunk_fill(int32_t nchunks, int L, const int32_t *c_row0,
                               const int64_t *rw_off, const int32_t *rw_col,
                               const double *rw_val, int4 *meta, int32_t *ecol, T *eval,
                               int32_t *row_id, T *diag, cudaStream_t s);
+// Export (tests): x terms (including run slots, decoded back to rows) and b
+// terms per original row.
 cudaError_t launch_export_count(int32_t nchunks, int L, const int4 *meta, const int32_t *ecol,
-                                const int32_t *row_id, int64_t *xcnt, int64_t *bcnt,
+                                const int32_t *row_id, int32_t n, int64_t *xcnt, int64_t *bcnt,
                                 cudaStream_t s);
 cudaError_t launch_export_fill(int32_t nchunks, int L, const int4 *meta, const int32_t *ecol,
                                const double *eval, const int32_t *row_id,
-                               const int32_t *chunk_level, const int64_t *xptr,
-                               const int64_t *bptr, int32_t *xcol, double *xval,
-                               int32_t *bcol, double *bw, int32_t *new_level, cudaStream_t s);
+                               const int32_t *chunk_level, const int32_t *chunk_run_p0,
+                               int32_t n, const int64_t *xptr, const int64_t *bptr,
+                               int32_t *xcol, double *xval, int32_t *bcol, double *bw,
+                               int32_t *new_level, cudaStream_t s);
 cudaError_t launch_chunk_level(int32_t nlev, const int32_t *lvl_chunk, int32_t *chunk_level,
                                cudaStream_t s);
 cudaError_t launch_f64_to_f32(const double *a, float *b, int64_t n, cudaStream_t s);
+// Encodes the x terms of run chunks that read a row of their own run as
+// shared-memory slots (see SolveData::run_slots).  pos_tmp: int32[n].
+cudaError_t launch_encode_runs(int32_t n, int L, const int32_t *row_id, const int4 *meta,
+                               int32_t nrc, const int32_t *run_chunk, const int2 *run_span,
+                               int32_t *pos_tmp, int32_t *ecol, cudaStream_t s);
 
 }  // namespace sptrsv
