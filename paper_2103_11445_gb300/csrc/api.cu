@@ -707,7 +707,7 @@ sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t 
             LaunchCfg lc{p->cfg.block_threads, grid_for(p, nr, false)};
             if (lc.grid <= 0) return SPTRSV_ERR_CUDA;
             CK(launch_solve<double>(sd, b + c0, x + c0, n, nrhs, nr, p->cfg.syncfree, lc,
-                                    p->status.p, tmo, false, s, /*prefilled=*/true));
+                                    p->status.p, tmo, false, s));
         }
         if (p->profiling) {
             CK(cudaEventRecord(p->prof_ev[1], s));

@@ -181,6 +181,7 @@ __device__ __forceinline__ bool chunk_one(const SolveData<T> &sd, int32_t c, T *
         r = __ldg(&sd.row_id[mt.x + k]);
         load_diag<T>(sd, mt.x + k, dg, dy);
         brow = (T)load_rhs(cx, (int64_t)r * cx.ld);
+        acc = brow;
     }
     if (active) {
         const int64_t stride = (int64_t)mt.y * L;
@@ -201,15 +202,18 @@ __device__ __forceinline__ bool chunk_one(const SolveData<T> &sd, int32_t c, T *
                 if (cc[u] >= 0) xv[u] = load_x<T, SF>(out + (int64_t)cc[u] * cx.ld);
                 else xv[u] = other_term<T>(cx, cc[u], out, 0);
             }
-            T pr[U];
+            // the row's sum runs from b_i down: terms already computed first,
+            // late arrivals last, so that each costs one dependent FMA
+            bool pend[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                if (SF && cc[u] >= 0 && Bits<T>::of(xv[u]) == Sentinel<T>::bits)
-                    xv[u] = wait_x<T>(out + (int64_t)cc[u] * cx.ld, cx.st, cx.timeout_ns, bail);
-                pr[u] = vv[u] * xv[u];
+                pend[u] = SF && cc[u] >= 0 && Bits<T>::of(xv[u]) == Sentinel<T>::bits;
+                if (!pend[u]) acc = fma(-vv[u], xv[u], acc);
             }
-            // fixed-order tree: few dependent FP64 operations after the last arrival
-            acc += (pr[0] + pr[1]) + (pr[2] + pr[3]);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (pend[u])
+                    acc = fma(-vv[u], wait_x<T>(out + (int64_t)cc[u] * cx.ld, cx.st, cx.timeout_ns, bail), acc);
         }
         for (; step < mt.z; ++step) {
             const int32_t cc = __ldg(cp + (int64_t)step * stride);
@@ -222,13 +226,13 @@ __device__ __forceinline__ bool chunk_one(const SolveData<T> &sd, int32_t c, T *
             } else {
                 xv = other_term<T>(cx, cc, out, 0);
             }
-            acc = fma(v, xv, acc);
+            acc = fma(-v, xv, acc);
         }
     }
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
     if (active && s == 0) {
-        const T res = div_by_diag<T>(brow - acc, dg, dy);
+        const T res = div_by_diag<T>(acc, dg, dy);
         store_x<T, SF>(out + (int64_t)r * cx.ld, res);
         keep_in_run<T>(cx, mt.x + k, res);
     }
@@ -520,17 +524,6 @@ solve_syncfree_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr
     for (int32_t c = gw; c < sd.nchunks; c += nw)
         if (process_chunk<T, L, R, true>(sd, c, out, cx)) break;
     grid_exit(st);
-}
-
-template <typename T>
-__global__ void fill_sentinel(T *out, int32_t n, int ld, int nr, DevStatus *st,
-                              int skip_if_converged) {
-    if (skip_if_converged && converged(st)) return;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t total = (int64_t)n * nr;
-    if (i >= total) return;
-    const int64_t row = i / nr, c = i % nr;
-    *reinterpret_cast<typename Bits<T>::U *>(out + row * ld + c) = Sentinel<T>::bits;
 }
 
 template <typename T, bool SF, int R>
@@ -827,29 +820,14 @@ template int max_coresident_ctas<double>(int, int, bool, int, int, int);
 template int max_coresident_ctas<float>(int, int, bool, int, int, int);
 
 template <typename T>
-cudaError_t launch_fill_sentinel(T *out, int32_t n, int ld, int nr, DevStatus *st,
-                                 bool skip_if_converged, cudaStream_t s) {
-    const int64_t total = (int64_t)n * nr;
-    if (total == 0) return cudaSuccess;
-    fill_sentinel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(out, n, ld, nr, st,
-                                                                     skip_if_converged ? 1 : 0);
-    return cudaGetLastError();
-}
-template cudaError_t launch_fill_sentinel<double>(double *, int32_t, int, int, DevStatus *, bool,
-                                                  cudaStream_t);
-template cudaError_t launch_fill_sentinel<float>(float *, int32_t, int, int, DevStatus *, bool,
-                                                 cudaStream_t);
-
-template <typename T>
 cudaError_t launch_solve(const SolveData<T> &sd, const double *rhs, T *out, int32_t n,
                          int ld, int nr, bool syncfree, const LaunchCfg &cfg,
                          DevStatus *st, uint64_t timeout_ns, bool skip_if_converged,
-                         cudaStream_t s, bool prefilled) {
+                         cudaStream_t s) {
     if (n == 0 || nr == 0) return cudaSuccess;
     const void *k = pick_kernel<T>(sd.L, nr, syncfree);
     if (!k) return cudaErrorInvalidValue;
     const int skip = skip_if_converged ? 1 : 0;
-    (void)prefilled;  // the synchronisation-free kernel fills its own sentinels
     SolveData<T> sdc = sd;
     void *args[] = {(void *)&sdc, (void *)&rhs,        (void *)&out,  (void *)&ld,
                     (void *)&nr,  (void *)&st,         (void *)&timeout_ns,
@@ -873,10 +851,10 @@ cudaError_t launch_solve(const SolveData<T> &sd, const double *rhs, T *out, int3
 }
 template cudaError_t launch_solve<double>(const SolveData<double> &, const double *, double *,
                                           int32_t, int, int, bool, const LaunchCfg &,
-                                          DevStatus *, uint64_t, bool, cudaStream_t, bool);
+                                          DevStatus *, uint64_t, bool, cudaStream_t);
 template cudaError_t launch_solve<float>(const SolveData<float> &, const double *, float *,
                                          int32_t, int, int, bool, const LaunchCfg &,
-                                         DevStatus *, uint64_t, bool, cudaStream_t, bool);
+                                         DevStatus *, uint64_t, bool, cudaStream_t);
 
 cudaError_t launch_residual(int32_t n, const int32_t *row_ptr, const int32_t *col,
                             const double *val, const double *b, const double *x, double *r,

@@ -49,11 +49,7 @@ template <typename T>
 cudaError_t launch_solve(const SolveData<T> &sd, const double *rhs, T *out, int32_t n,
                          int ld, int nr, bool syncfree, const LaunchCfg &cfg,
                          DevStatus *st, uint64_t timeout_ns, bool skip_if_converged,
-                         cudaStream_t s, bool prefilled = false);
-// Sentinel pre-fill of the synchronisation-free solve's output.
-template <typename T>
-cudaError_t launch_fill_sentinel(T *out, int32_t n, int ld, int nr, DevStatus *st,
-                                 bool skip_if_converged, cudaStream_t s);
+                         cudaStream_t s);
 
 // Largest co-resident grid for the chosen kernel (CTAs per SM * SMs), with
 // the dynamic shared memory the barrier kernel's runs need.
