@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--mode", choices=["barrier", "syncfree"], default="syncfree")
     ap.add_argument("--lanes", type=int, default=4)
     ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--grid", type=int, default=0, help="profile-run grid (0: largest co-resident)")
     return ap.parse_args()
 
 
@@ -272,7 +273,7 @@ def run_profile(args):
     P = Bd.Plan(A.n, A.row_ptr, A.col, A.val)
     mode = Bd.SOLVE_SYNCFREE if args.mode == "syncfree" else Bd.SOLVE_BARRIER
     P.transform(solve_mode=mode, lanes_per_row=args.lanes, block_threads=args.block,
-                cta_run_rows=-1, **select_kw(args.select, Bd))
+                grid_blocks=args.grid, cta_run_rows=-1, **select_kw(args.select, Bd))
     b = torch.as_tensor(b_np, device=dev)
     x = torch.empty_like(b)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -356,7 +357,7 @@ def run_ours(args, world, rank, local):
                              nlev_new=info["nlev_new"], flops_new=info["flops_new"],
                              solve_mode=info["solve_mode"], L=info["lanes_per_row"],
                              block=info["block_threads"], grid=info["grid_blocks"],
-                             cta_run_rows=info["cta_run_rows"])
+                             cta_run_rows=info["cta_run_rows"], backoff=info["poll_backoff_ns"])
     # the learned cost model's own pick (weights trained on the solver's timings)
     cm_info = None
     try:
@@ -375,14 +376,24 @@ def run_ours(args, world, rank, local):
                                         nlev_new=info["nlev_new"], flops_new=info["flops_new"],
                                         solve_mode=info["solve_mode"], L=info["lanes_per_row"],
                                         block=info["block_threads"], grid=info["grid_blocks"],
-                                        cta_run_rows=info["cta_run_rows"])
+                                        cta_run_rows=info["cta_run_rows"],
+                                        backoff=info["poll_backoff_ns"])
     except Exception as exc:  # the weights are optional; report why they were not used
         cm_info = dict(error=str(exc)[:200])
     rewritten = {k: v for k, v in results.items() if k != "plain"}
     best = min(rewritten, key=lambda k: rewritten[k]["ms"])
 
+    def tuned(name):
+        """The candidate's selection with the launch configuration its own
+        autotuning chose, pinned, so the timed runs repeat exactly that."""
+        r = results[name]
+        return dict(r["kw"], solve_mode=r["solve_mode"], lanes_per_row=r["L"],
+                    block_threads=r["block"], grid_blocks=r["grid"],
+                    cta_run_rows=r["cta_run_rows"] if r["cta_run_rows"] > 0 else -1,
+                    poll_backoff_ns=r["backoff"])
+
     def measure(kw, steps, warmup, label):
-        P.transform(solve_mode=Bd.SOLVE_AUTO, **kw)
+        P.transform(**kw)
         info = P.info()
         barrier(world)
         torch.cuda.synchronize()
@@ -398,11 +409,11 @@ def run_ours(args, world, rank, local):
     clocks = ClockSampler(uuid)
     clocks.start()
     # plain level-set, same protocol
-    pinfo, p_steps, p_kern = measure(results["plain"]["kw"], args.steps, args.warmup, "plain")
+    pinfo, p_steps, p_kern = measure(tuned("plain"), args.steps, args.warmup, "plain")
     plain_ms = max_over_ranks(world, statistics.mean(p_steps))
 
     # headline: rewritten, autotuned
-    info, steps_ms, kern_ms = measure(rewritten[best]["kw"], args.steps, args.warmup, best)
+    info, steps_ms, kern_ms = measure(tuned(best), args.steps, args.warmup, best)
     clk = clocks.stop()
     ms = max_over_ranks(world, statistics.mean(steps_ms))
     value = B * world / (ms * 1e-3) / 1e9

@@ -573,11 +573,16 @@ sptrsv_status_t apply_config(sptrsv_plan_t p, cudaStream_t s) {
 sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t nrhs,
                            cudaStream_t s);
 
-// Times candidate launch configurations on the plan (median of 5 solves)
-// and keeps the fastest.
+// Times candidate launch configurations on the plan (median of a few solves)
+// and keeps the fastest.  Stage 1 crosses lanes per row with the three
+// execution modes (grid barrier, barrier + CTA-local runs, synchronisation
+// free) at three launch shapes; stage 2 sweeps the launch shape of the two
+// best (lanes, mode) pairs; stage 3 the polling back-off of the sync-free
+// kernel.  Trials of long solves use fewer repetitions.
 sptrsv_status_t autotune(sptrsv_plan_t p, cudaStream_t s) {
     const int32_t n = p->n;
     if (n == 0) return SPTRSV_OK;
+    const bool f32 = p->prm.precision == SPTRSV_F32_IR;
     DevArr<double> b, x;
     CK(b.alloc(n));
     CK(x.alloc(n));
@@ -586,11 +591,12 @@ sptrsv_status_t autotune(sptrsv_plan_t p, cudaStream_t s) {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    int warm = 2, reps = 5;
     auto time_cfg = [&](double *ms_out) -> sptrsv_status_t {
         CKS(apply_config(p, s));
-        for (int w = 0; w < 2; ++w) CKS(solve_impl(p, b.p, x.p, 1, s));
+        for (int w = 0; w < warm; ++w) CKS(solve_impl(p, b.p, x.p, 1, s));
         std::vector<float> t;
-        for (int r = 0; r < 5; ++r) {
+        for (int r = 0; r < reps; ++r) {
             CK(cudaEventRecord(e0, s));
             CKS(solve_impl(p, b.p, x.p, 1, s));
             CK(cudaEventRecord(e1, s));
@@ -604,64 +610,95 @@ sptrsv_status_t autotune(sptrsv_plan_t p, cudaStream_t s) {
         *ms_out = t[t.size() / 2];
         return SPTRSV_OK;
     };
+    struct Trial {
+        SolveConfig c;
+        double ms;
+    };
+    std::vector<Trial> tried;
+    auto same = [](const SolveConfig &a, const SolveConfig &c) {
+        return a.L == c.L && a.syncfree == c.syncfree && a.block_threads == c.block_threads &&
+               a.grid == c.grid && a.cta_run_rows == c.cta_run_rows &&
+               a.backoff_ns == c.backoff_ns;
+    };
     SolveConfig best = p->cfg;
     double best_ms = 1e30;
+    auto trial = [&](const SolveConfig &c, double *ms) -> sptrsv_status_t {
+        for (const Trial &t : tried)
+            if (same(t.c, c)) {
+                *ms = t.ms;
+                return SPTRSV_OK;
+            }
+        *ms = 1e30;
+        p->cfg = c;
+        if (c.grid > 0 && grid_for(p, 1, f32) < c.grid) return SPTRSV_OK;  // not co-resident
+        CKS(time_cfg(ms));
+        tried.push_back({c, *ms});
+        if (*ms > 5.0) {  // long solves: fewer repetitions
+            warm = 1;
+            reps = 3;
+        }
+        if (*ms < best_ms) {
+            best_ms = *ms;
+            best = c;
+        }
+        return SPTRSV_OK;
+    };
+    const int bt_req = p->prm.block_threads;
+    const int grid_req = p->prm.grid_blocks;
+    const int backoff0 = p->prm.poll_backoff_ns > 0 ? p->prm.poll_backoff_ns : 0;
+    auto shaped = [&](SolveConfig c, int bt, int per_sm) {
+        c.block_threads = bt_req > 0 ? bt_req : bt;
+        c.grid = grid_req > 0 ? grid_req : per_sm * p->num_sms;
+        if (c.cta_run_rows > 0) c.cta_run_rows = c.block_threads / c.L;
+        return c;
+    };
     std::vector<int> lanes = {1, 2, 4};
     const int la = auto_lanes(p);
     if (la > 4) lanes.push_back(la);
-    const int bt_req = p->prm.block_threads;
+    // stage 1: lanes x mode at three launch shapes
+    struct Pair {
+        SolveConfig c;
+        double ms;
+    };
+    std::vector<Pair> pairs;
     for (int L : lanes) {
         if (p->prm.lanes_per_row > 0 && L != p->prm.lanes_per_row) continue;
         for (int mode = 0; mode < 3; ++mode) {
+            if (p->prm.cta_run_rows < 0 && mode == 1) continue;
             SolveConfig c;
             c.L = L;
             c.syncfree = mode == 2;
-            c.block_threads = bt_req > 0 ? bt_req : 512;
-            c.grid = p->prm.grid_blocks > 0 ? p->prm.grid_blocks : (c.syncfree ? 0 : p->num_sms);
-            c.backoff_ns = p->prm.poll_backoff_ns > 0 ? p->prm.poll_backoff_ns : 0;
-            c.cta_run_rows = mode == 1 ? c.block_threads / L : 0;
-            if (p->prm.cta_run_rows < 0 && mode == 1) continue;
-            p->cfg = c;
-            double ms;
-            CKS(time_cfg(&ms));
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = c;
+            c.backoff_ns = backoff0;
+            c.cta_run_rows = mode == 1 ? 1 : 0;  // set from the block size by shaped()
+            double pm = 1e30;
+            for (const auto &sh : {std::make_pair(128, 4), std::make_pair(128, 8),
+                                   std::make_pair(512, 1)}) {
+                double ms;
+                CKS(trial(shaped(c, sh.first, sh.second), &ms));
+                pm = std::min(pm, ms);
             }
+            pairs.push_back({c, pm});
         }
     }
-    // polling back-off of the synchronisation-free kernel
+    std::sort(pairs.begin(), pairs.end(),
+              [](const Pair &a, const Pair &c) { return a.ms < c.ms; });
+    // stage 2: launch shape of the two best pairs
+    for (size_t i = 0; i < pairs.size() && i < 2; ++i) {
+        if (pairs[i].ms >= 1e30) break;
+        for (int bt : {128, 256, 512})
+            for (int per_sm : {1, 2, 4, 8}) {
+                double ms;
+                CKS(trial(shaped(pairs[i].c, bt, per_sm), &ms));
+            }
+    }
+    // stage 3: polling back-off of the synchronisation-free kernel
     if (best.syncfree && p->prm.poll_backoff_ns < 0) {
         const SolveConfig b0 = best;
         for (int ns : {32, 128, 512}) {
             SolveConfig c = b0;
             c.backoff_ns = ns;
-            p->cfg = c;
             double ms;
-            CKS(time_cfg(&ms));
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = c;
-            }
-        }
-    }
-    // launch shape around the best layout and mode
-    const SolveConfig base = best;
-    for (int bt : {128, 256, 512}) {
-        if (bt_req > 0 && bt != bt_req) continue;
-        for (int per_sm : {1, 2, 4, 8}) {
-            SolveConfig c = base;
-            c.block_threads = bt;
-            c.grid = per_sm * p->num_sms;
-            if (c.cta_run_rows > 0) c.cta_run_rows = bt / c.L;
-            p->cfg = c;
-            if (grid_for(p, 1, p->prm.precision == SPTRSV_F32_IR) < c.grid) continue;
-            double ms;
-            CKS(time_cfg(&ms));
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = c;
-            }
+            CKS(trial(c, &ms));
         }
     }
     cudaEventDestroy(e0);

@@ -62,22 +62,45 @@ __device__ __forceinline__ T load_x(const T *p) {
 }
 
 // Bounded spin until *p holds a computed value (synchronisation-free only).
+// Returns the value's bits; the sentinel's bits mean the wait gave up (a
+// computed value never has them: stores turn them into a quiet NaN).  The
+// out-of-line copy keeps the spin loop out of the hot path, and returning
+// the status by value keeps the caller's flag in a register.
 template <typename T>
-__device__ __forceinline__ T wait_x_inl(const T *p, DevStatus *st, uint64_t timeout_ns,
-                                        int backoff_ns, bool &bail) {
+__device__ __forceinline__ typename Bits<T>::U wait_bits_inl(const T *p, DevStatus *st,
+                                                            uint64_t timeout_ns, int backoff_ns) {
     WaitBudget wb(timeout_ns);
     unsigned it = 0;
     typename Bits<T>::U b;
     do {
         if (backoff_ns) __nanosleep(backoff_ns);
-        if ((++it & kPollMask) == 0 && wb.expired(st, -2)) { bail = true; return T(0); }
+        if ((++it & kPollMask) == 0 && wb.expired(st, -2)) return Sentinel<T>::bits;
         b = Bits<T>::poll(p);
     } while (b == Sentinel<T>::bits);
+    return b;
+}
+template <typename T>
+__device__ __noinline__ typename Bits<T>::U wait_bits(const T *p, DevStatus *st,
+                                                     uint64_t timeout_ns, int backoff_ns) {
+    return wait_bits_inl<T>(p, st, timeout_ns, backoff_ns);
+}
+template <typename T>
+__device__ __forceinline__ T bits_or_bail(typename Bits<T>::U b, bool &bail) {
+    if (b == Sentinel<T>::bits) {
+        bail = true;
+        return T(0);
+    }
     return Bits<T>::from(b);
 }
 template <typename T>
-__device__ __noinline__ T wait_x(const T *p, DevStatus *st, uint64_t timeout_ns, bool &bail) {
-    return wait_x_inl<T>(p, st, timeout_ns, 0, bail);
+__device__ __forceinline__ T wait_x(const T *p, DevStatus *st, uint64_t timeout_ns,
+                                    int backoff_ns, bool &bail) {
+    return bits_or_bail<T>(wait_bits<T>(p, st, timeout_ns, backoff_ns), bail);
+}
+template <typename T>
+__device__ __forceinline__ T wait_x_inl(const T *p, DevStatus *st, uint64_t timeout_ns,
+                                        int backoff_ns, bool &bail) {
+    return bits_or_bail<T>(wait_bits_inl<T>(p, st, timeout_ns, backoff_ns), bail);
 }
 
 template <typename T, bool SF>
@@ -96,24 +119,31 @@ __device__ __forceinline__ void store_x(T *p, T v) {
 // (|s| in [slo, shi)) and the result away from underflow and overflow
 // (|q| in [qlo, qhi)); everything else takes an IEEE division.
 template <typename T> struct DivRange;
-template <> struct DivRange<double> {
-    static constexpr double slo = 0x1p-900, shi = 0x1p+900;
-    static constexpr double qlo = 0x1p-1000, qhi = 0x1p+1000;
+template <> struct DivRange<double> {  // bit patterns of 2^-900, 2^900, 2^-1000, 2^1000
+    static constexpr unsigned long long abs = 0x7FFFFFFFFFFFFFFFull;
+    static constexpr unsigned long long slo = 0x07B0000000000000ull, shi = 0x7830000000000000ull;
+    static constexpr unsigned long long qlo = 0x0170000000000000ull, qhi = 0x7E70000000000000ull;
 };
-template <> struct DivRange<float> {
-    static constexpr float slo = 0x1p-100f, shi = 0x1p+100f;
-    static constexpr float qlo = 0x1p-120f, qhi = 0x1p+120f;
+template <> struct DivRange<float> {  // bit patterns of 2^-100, 2^100, 2^-120, 2^120
+    static constexpr unsigned abs = 0x7FFFFFFFu;
+    static constexpr unsigned slo = 0x0D800000u, shi = 0x71800000u;
+    static constexpr unsigned qlo = 0x03800000u, qhi = 0x7B800000u;
 };
 
+// The range tests compare bit patterns as integers (for non-negative
+// floating-point numbers the order is the same, and NaN lies above every
+// bound), which keeps them off the FP64 pipe: on this GPU every FP64
+// instruction is a scarce resource.
 template <typename T>
 __device__ __forceinline__ T div_by_diag(T s, T d, T y) {
-    const T as = fabs(s);
-    if (y != T(0) && as >= DivRange<T>::slo && as < DivRange<T>::shi) {
+    using R = DivRange<T>;
+    const auto as = Bits<T>::of(s) & R::abs;
+    if (Bits<T>::of(y) != 0 && as - R::slo < R::shi - R::slo) {
         const T q = s * y;
         const T r = fma(-q, d, s);
         const T q2 = fma(r, y, q);
-        const T a = fabs(q2);
-        if (a >= DivRange<T>::qlo && a < DivRange<T>::qhi) return q2;
+        const auto a = Bits<T>::of(q2) & R::abs;
+        if (a - R::qlo < R::qhi - R::qlo) return q2;
     }
     return s / d;
 }
@@ -213,7 +243,7 @@ __device__ __forceinline__ bool chunk_one(const SolveData<T> &sd, int32_t c, T *
 #pragma unroll
             for (int u = 0; u < U; ++u)
                 if (pend[u])
-                    acc = fma(-vv[u], wait_x<T>(out + (int64_t)cc[u] * cx.ld, cx.st, cx.timeout_ns, bail), acc);
+                    acc = fma(-vv[u], wait_x<T>(out + (int64_t)cc[u] * cx.ld, cx.st, cx.timeout_ns, cx.backoff_ns, bail), acc);
         }
         for (; step < mt.z; ++step) {
             const int32_t cc = __ldg(cp + (int64_t)step * stride);
@@ -222,7 +252,7 @@ __device__ __forceinline__ bool chunk_one(const SolveData<T> &sd, int32_t c, T *
             if (cc >= 0) {
                 xv = load_x<T, SF>(out + (int64_t)cc * cx.ld);
                 if (SF && Bits<T>::of(xv) == Sentinel<T>::bits)
-                    xv = wait_x<T>(out + (int64_t)cc * cx.ld, cx.st, cx.timeout_ns, bail);
+                    xv = wait_x<T>(out + (int64_t)cc * cx.ld, cx.st, cx.timeout_ns, cx.backoff_ns, bail);
             } else {
                 xv = other_term<T>(cx, cc, out, 0);
             }
@@ -261,6 +291,7 @@ __device__ __forceinline__ bool chunk_multi(const SolveData<T> &sd, int32_t c, T
             row = __ldg(&sd.row_id[mt.x + k]);
             load_diag<T>(sd, mt.x + k, dg, dy);
             brow = (T)load_rhs(cx, (int64_t)row * cx.ld + r);
+            acc = brow;
         }
         if (rowok) {
             const int64_t base = mt.w + (int64_t)k * L;
@@ -275,16 +306,16 @@ __device__ __forceinline__ bool chunk_multi(const SolveData<T> &sd, int32_t c, T
                         T *px = out + (int64_t)cc * cx.ld + r;
                         xv = load_x<T, SF>(px);
                         if (SF && Bits<T>::of(xv) == Sentinel<T>::bits)
-                            xv = wait_x<T>(px, cx.st, cx.timeout_ns, bail);
+                            xv = wait_x<T>(px, cx.st, cx.timeout_ns, cx.backoff_ns, bail);
                     } else {
                         xv = other_term<T>(cx, cc, out, r);
                     }
-                    acc = fma(v, xv, acc);
+                    acc = fma(-v, xv, acc);
                 }
             }
         }
         if (active)
-            store_x<T, SF>(out + (int64_t)row * cx.ld + r, div_by_diag<T>(brow - acc, dg, dy));
+            store_x<T, SF>(out + (int64_t)row * cx.ld + r, div_by_diag<T>(acc, dg, dy));
         if (__any_sync(FULL_MASK, bail)) return true;
     }
     return false;
@@ -355,20 +386,21 @@ __device__ __forceinline__ bool finish_staged(const SolveData<T> &sd, const Stag
         else xv[u] = other_term<T>(cx, c, out, 0);
     }
     bool bail = false;
-    T pr[kPipeSteps];
+    // the sum runs from b_i down, one FMA per staged step (FP64 instructions
+    // are the scarce resource: no separate products, no tree)
+    T acc = brow;
 #pragma unroll
     for (int u = 0; u < kPipeSteps; ++u) {
+        if (u >= sg.mt.z) break;
         if (SF && sg.col[u] >= 0 && Bits<T>::of(xv[u]) == Sentinel<T>::bits)
             xv[u] = wait_x_inl<T>(out + (int64_t)sg.col[u] * cx.ld, cx.st, cx.timeout_ns,
                                   cx.backoff_ns, bail);
-        pr[u] = sg.val[u] * xv[u];
+        acc = fma(-sg.val[u], xv[u], acc);
     }
-    // short dependency chain after the last arrival (FP64 latency is long)
-    T acc = (pr[0] + pr[1]) + (pr[2] + pr[3]);
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
     if (active && s == 0) {
-        const T res = div_by_diag<T>(brow - acc, sg.diag, sg.rdiag);
+        const T res = div_by_diag<T>(acc, sg.diag, sg.rdiag);
         store_x<T, SF>(out + (int64_t)sg.row * cx.ld, res);
         keep_in_run<T>(cx, sg.mt.x + k, res);
     }
@@ -503,12 +535,11 @@ solve_syncfree_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr
     // every unknown of this launch starts as the "not computed" sentinel; one
     // grid barrier orders those stores before any poll
     {
-        const int64_t total = (int64_t)sd.n * nr;
-        const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gthreads) {
-            const int64_t row = i / nr, col = i % nr;
-            *reinterpret_cast<typename Bits<T>::U *>(out + row * ld + col) = Sentinel<T>::bits;
-        }
+        const int32_t gthreads = gridDim.x * blockDim.x;
+        for (int32_t row = blockIdx.x * blockDim.x + threadIdx.x; row < sd.n; row += gthreads)
+            for (int c = 0; c < nr; ++c)
+                *reinterpret_cast<typename Bits<T>::U *>(out + (int64_t)row * ld + c) =
+                    Sentinel<T>::bits;
     }
     if (!grid_barrier(st, gridDim.x, timeout_ns, -5)) {
         grid_exit(st);
@@ -654,7 +685,15 @@ template <typename T>
 __device__ __forceinline__ bool batch_chunk(const SolveData<T> &sd, int32_t c, T *out,
                                             const Ctx &cx, int R) {
     switch (R) {
-    case 1: return chunk_multi<T, 1, true>(sd, c, out, cx);
+    case 1:  // one right-hand side: the lanes-per-row chunk processor
+        switch (sd.L) {
+        case 1: return chunk_one<T, 1, true>(sd, c, out, cx);
+        case 2: return chunk_one<T, 2, true>(sd, c, out, cx);
+        case 4: return chunk_one<T, 4, true>(sd, c, out, cx);
+        case 8: return chunk_one<T, 8, true>(sd, c, out, cx);
+        case 16: return chunk_one<T, 16, true>(sd, c, out, cx);
+        default: return chunk_one<T, 32, true>(sd, c, out, cx);
+        }
     case 2: return chunk_multi<T, 2, true>(sd, c, out, cx);
     case 4: return chunk_multi<T, 4, true>(sd, c, out, cx);
     case 8: return chunk_multi<T, 8, true>(sd, c, out, cx);
