@@ -101,9 +101,10 @@ def solve_source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_tag: str):
+def profiled_traffic(kernel_tag: str, selection: str, lanes: int):
     """Per-launch DRAM bytes of the timed kernel from the committed ncu
-    summary, if that summary was taken on the current kernel source."""
+    summary, if that summary was taken on the current kernel source and on
+    the same selection and lanes per row as the timed plan."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}_{WORKLOAD}.md")
     if not os.path.exists(path):
         return None
@@ -114,6 +115,8 @@ def profiled_traffic(kernel_tag: str):
                 k, v = line.strip()[2:].split(":", 1)
                 vals[k.strip()] = v.strip().strip("`")
     if vals.get("source_digest") != solve_source_digest():
+        return None
+    if vals.get("selection") != selection or vals.get("lanes_per_row") != str(lanes):
         return None
     try:
         return int(vals["dram_bytes_per_launch"])
@@ -479,7 +482,7 @@ def run_ours(args, world, rank, local):
                      "peak_kind": f"{peak_kind} copy bandwidth",
                      "kernel": f"{kernel_tag} (mean of {len(kern_ms)} launches, "
                                f"{kern_mean * 1e3:.1f} us, CUDA events on the launch stream)",
-                     "traffic": profiled_traffic(kernel_tag)},
+                     "traffic": profiled_traffic(kernel_tag, best, info["lanes_per_row"])},
         "e2e": {"value": round(e2e_val, 3), "unit": "GB/s", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": launches_per_solve * args.steps,
