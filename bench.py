@@ -445,6 +445,10 @@ def run_ours(args, world, rank, local):
     P.check()
     e2e_val = B * world / (max_over_ranks(world, statistics.mean(e2e_ms)) * 1e-3) / 1e9
     launches_per_solve = 1
+    moved = 12 * (info["nnz_x"] + info["nnz_b"] + n) + 4 * (n + 1) + 16 * n
+    saved_ms = plain_ms - ms
+    break_even = (round(rewritten[best]["transform_ms"] / saved_ms, 1) if saved_ms > 0
+                  else None)
 
     line = {
         "metric": "SpTRSV eff. GB/s (B_alg / t_solve), rewritten + autotuned, FP64",
@@ -463,7 +467,12 @@ def run_ours(args, world, rank, local):
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
             "analyze_ms": round(analyze_ms, 2),
             "transform_ms": round(rewritten[best]["transform_ms"], 2),
+            # bytes the transformed plan reads and writes per solve by the same
+            # formula as B_alg (12 B per x or b term plus the row terms)
+            "moved_bytes": moved,
+            "break_even_solves": break_even,
         },
+        "hbm_frac_of_nominal_8tbs": round(achieved / 8000.0, 4),
         "plain_levelset": {
             "value": round(B * world / (plain_ms * 1e-3) / 1e9, 3), "unit": "GB/s",
             "ms_per_step": round(plain_ms, 5),

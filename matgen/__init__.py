@@ -235,6 +235,19 @@ def random_lower(n: int, seed: int, density: float = 0.3,
     return _from_row_lists(n, cols, vals, diag)
 
 
+def transposed(A: CSR) -> CSR:
+    """The same entries stored as A^T (a lower matrix becomes an upper one):
+    entries ordered by (column, row) with a stable sort, CSR of the result
+    (an input rearrangement, no arithmetic on the values)."""
+    rows = np.repeat(np.arange(A.n, dtype=np.int64), np.diff(A.row_ptr))
+    order = np.lexsort((rows, A.col))
+    cnt = np.bincount(A.col, minlength=A.n)
+    ptr = np.zeros(A.n + 1, np.int64)
+    np.cumsum(cnt, out=ptr[1:])
+    return CSR(A.n, ptr.astype(np.int32), rows[order].astype(np.int32),
+               np.ascontiguousarray(A.val[order]))
+
+
 def rhs_uniform(n: int, nrhs: int = 1, seed: int = 7) -> np.ndarray:
     """b ~ U[-1, 1], row-major [n, nrhs] (shape [n] when nrhs == 1)."""
     rng = np.random.default_rng(seed)

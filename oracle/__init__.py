@@ -12,6 +12,10 @@ Contents (each function cites the passage of the paper it follows):
   Algorithm 1) -- C, ``sptrsv_oracle.c``;
 * ``levels``         level of every row in DAG_L (Sec. II) -- C;
 * ``residual``       r = b - L x -- C;
+* ``backward_subst`` serial FP64 CSR backward substitution for an upper
+  triangle (the mirror image of Algorithm 1) -- C;
+* ``transpose``      CSR of A^T (scipy.sparse) and ``solve_op``: L x = b,
+  U x = b, L^T x = b or U^T x = b by the substitution that operator needs;
 * ``rewrite``        equation rewriting of one row (Sec. III, Figs. 2-3) and
   the thin-level selection heuristic -- Python, ``rewrite.py``;
 * ``mlp``            FP64 forward/backward/Adam of the 3-layer cost-model
@@ -65,15 +69,21 @@ def _load():
                                           ctypes.POINTER(ctypes.c_int32)]
             lib.oracle_spmv_lower.argtypes = [ctypes.c_int32, i32p, i32p, f64p,
                                               f64p, f64p, f64p, ctypes.c_int32]
+            lib.oracle_backward_subst.argtypes = [ctypes.c_int32, i32p, i32p,
+                                                  f64p, f64p, f64p,
+                                                  ctypes.c_int32]
             for f in (lib.oracle_forward_subst, lib.oracle_levels,
-                      lib.oracle_spmv_lower):
+                      lib.oracle_spmv_lower, lib.oracle_backward_subst):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
 
 
-_ERR = {1: "column out of range or above the diagonal",
+_ERR = {1: "column out of range or on the wrong side of the diagonal",
         2: "missing diagonal", 3: "zero diagonal"}
+
+# which triangular operator a CSR stands for (same numbering as the library)
+OP_LOWER, OP_UPPER, OP_LOWER_TRANS, OP_UPPER_TRANS = 0, 1, 2, 3
 
 
 def _csr(A):
@@ -93,6 +103,41 @@ def forward_subst(A, b: np.ndarray) -> np.ndarray:
     if rc:
         raise ValueError(_ERR[rc])
     return x.reshape(np.shape(b))
+
+
+def backward_subst(U, b: np.ndarray) -> np.ndarray:
+    """x = U^{-1} b for an upper-triangular CSR by serial backward
+    substitution (rows from last to first)."""
+    rp, c, v = _csr(U)
+    b2 = np.ascontiguousarray(b, np.float64).reshape(U.n, -1)
+    x = np.empty_like(b2)
+    rc = _load().oracle_backward_subst(U.n, rp, c, v, b2, x, b2.shape[1])
+    if rc:
+        raise ValueError(_ERR[rc])
+    return x.reshape(np.shape(b))
+
+
+def transpose(A):
+    """CSR of A^T with ascending columns in every row (scipy.sparse)."""
+    import scipy.sparse as sp
+    M = sp.csr_matrix((A.val, A.col, A.row_ptr), shape=(A.n, A.n)).T.tocsr()
+    M.sort_indices()
+    return type(A)(A.n, M.indptr.astype(np.int32), M.indices.astype(np.int32),
+                   M.data.astype(np.float64))
+
+
+def solve_op(A, b: np.ndarray, op: int) -> np.ndarray:
+    """Solution of op(A) x = b: A x for OP_LOWER / OP_UPPER, A^T x for the
+    transposed operators, each by the substitution its triangle needs."""
+    if op == OP_LOWER:
+        return forward_subst(A, b)
+    if op == OP_UPPER:
+        return backward_subst(A, b)
+    if op == OP_LOWER_TRANS:
+        return backward_subst(transpose(A), b)
+    if op == OP_UPPER_TRANS:
+        return forward_subst(transpose(A), b)
+    raise ValueError(f"unknown operator {op}")
 
 
 def levels(A) -> tuple[np.ndarray, int]:

@@ -15,6 +15,9 @@
  *     longest dependency path that ends at the row, sources at level 0.
  *   - oracle_spmv_lower: r = b - L x, the residual used by the refinement
  *     checks.
+ *   - oracle_backward_subst: the same substitution for an upper-triangular
+ *     matrix, rows visited from the last to the first (the mirror image of
+ *     Algorithm 1: row i needs the unknowns of rows j > i).
  *
  * CSR convention: row_ptr[n+1], col[nnz] ascending inside each row,
  * val[nnz]; every row stores its diagonal.  Right-hand sides and solutions
@@ -92,6 +95,37 @@ int oracle_spmv_lower(int32_t n, const int32_t *row_ptr, const int32_t *col,
                 s -= val[k] * x[(size_t)j * nrhs + c];
             }
             r[(size_t)i * nrhs + c] = s;
+        }
+    }
+    return 0;
+}
+
+/* Backward substitution over an upper-triangular CSR (every stored column
+ * j >= i, diagonal stored): rows from n-1 down to 0, the row's off-diagonal
+ * products subtracted in ascending column order, then the division by the
+ * diagonal.  Same return codes, 1 meaning a column below the diagonal. */
+int oracle_backward_subst(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                          const double *val, const double *b, double *x,
+                          int32_t nrhs)
+{
+    for (int32_t r = 0; r < nrhs; ++r) {
+        for (int32_t i = n - 1; i >= 0; --i) {
+            double sum = b[(size_t)i * nrhs + r];
+            double diag = 0.0;
+            int have_diag = 0;
+            for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                int32_t j = col[k];
+                if (j < i || j >= n) return 1;
+                if (j == i) {
+                    diag = val[k];
+                    have_diag = 1;
+                } else {
+                    sum -= val[k] * x[(size_t)j * nrhs + r];
+                }
+            }
+            if (!have_diag) return 2;
+            if (diag == 0.0) return 3;
+            x[(size_t)i * nrhs + r] = sum / diag;
         }
     }
     return 0;

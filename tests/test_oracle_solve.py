@@ -135,5 +135,5 @@ def test_invalid_inputs_rejected():
         oracle.forward_subst(nodiag, np.ones(2))
     upper = mg.CSR(2, np.array([0, 2, 3], np.int32), np.array([0, 1, 1], np.int32),
                    np.ones(3))
-    with pytest.raises(ValueError, match="above the diagonal"):
+    with pytest.raises(ValueError, match="wrong side of the diagonal"):
         oracle.forward_subst(upper, np.ones(2))
