@@ -140,6 +140,7 @@ typedef struct {
     int32_t chosen_depth;    /* SELECT_COSTMODEL: depth the network picked
                                 (-1 when it did not run) */
     double analyze_ms, transform_ms;
+    int32_t op;              /* SPTRSV_OP_* of the plan */
 } sptrsv_info_t;
 
 SPTRSV_API const char *sptrsv_status_string(sptrsv_status_t s);
@@ -154,6 +155,35 @@ SPTRSV_API void sptrsv_default_params(sptrsv_transform_params_t *prm);
 SPTRSV_API sptrsv_status_t sptrsv_analyze(int32_t n, int64_t nnz, const int32_t *d_row_ptr,
                                const int32_t *d_col, const double *d_val,
                                sptrsv_stream_t stream, sptrsv_plan_t *out);
+
+/* Which triangular system a plan solves, given the CSR of A. */
+typedef enum {
+    SPTRSV_OP_LOWER = 0,        /* A lower triangular: A x = b (sptrsv_analyze) */
+    SPTRSV_OP_UPPER = 1,        /* A upper triangular: A x = b */
+    SPTRSV_OP_LOWER_TRANS = 2,  /* A lower triangular: A^T x = b */
+    SPTRSV_OP_UPPER_TRANS = 3   /* A upper triangular: A^T x = b */
+} sptrsv_op_t;
+
+/* sptrsv_analyze for any of the four operators.  The paper treats the lower
+ * triangle (Sec. II); the others are the same method on a mirrored system:
+ * op(A) is brought on the device to the lower triangle L' that Sec. II's
+ * forward substitution solves -- A^T by a CSR transpose (stable sort of the
+ * entries by column), an upper triangle U by the exchange permutation P,
+ * L' = P U P (so U x = b is L' (P x) = P b, the backward substitution).  The
+ * analysis, the rewriting (Sec. III) and the solve then run on L', and the
+ * solve structure is mirrored back once, so sptrsv_solve reads b and writes
+ * x in A's row order with no extra copies.
+ *   op       one of sptrsv_op_t (SPTRSV_ERR_INVALID_ARG otherwise).
+ *   CSR      as for sptrsv_analyze; every row stores its diagonal, columns
+ *            strictly ascending, A triangular in the sense op names.
+ * Errors: SPTRSV_ERR_NOT_LOWER means an entry on the wrong side of the
+ * diagonal for op (or a column outside [0, n)); the other validation codes
+ * as for sptrsv_analyze.  Inspection calls (sptrsv_get_levels,
+ * sptrsv_get_transformed) report rows and columns in A's numbering;
+ * sptrsv_get_segments reports the levels of L'. */
+SPTRSV_API sptrsv_status_t sptrsv_analyze_ex(int32_t n, int64_t nnz, const int32_t *d_row_ptr,
+                                  const int32_t *d_col, const double *d_val, int32_t op,
+                                  sptrsv_stream_t stream, sptrsv_plan_t *out);
 
 /* Equation rewriting (Sec. III, Figs. 2-3): select rows (prm->select_mode),
  * compute on the device the fill of every candidate rewrite, the rewritten

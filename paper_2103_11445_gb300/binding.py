@@ -27,6 +27,7 @@ STATUS_NAMES = {
 SELECT_NONE, SELECT_HEURISTIC, SELECT_COSTMODEL, SELECT_FIXED = 0, 1, 2, 3
 SOLVE_AUTO, SOLVE_BARRIER, SOLVE_SYNCFREE = 0, 1, 2
 F64, F32_IR = 0, 1
+OP_LOWER, OP_UPPER, OP_LOWER_TRANS, OP_UPPER_TRANS = 0, 1, 2, 3
 
 
 class SptrsvError(RuntimeError):
@@ -59,7 +60,7 @@ class Info(Structure):
         ("thin_rows", c_int32), ("max_depth", c_int32), ("flop_budget", c_double),
         ("ir_iters_last", c_int32), ("num_sms", c_int32), ("poll_backoff_ns", c_int32),
         ("chosen_depth", c_int32),
-        ("analyze_ms", c_double), ("transform_ms", c_double),
+        ("analyze_ms", c_double), ("transform_ms", c_double), ("op", c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -75,6 +76,8 @@ _SIGS = {
     "sptrsv_default_params": (None, [POINTER(TransformParams)]),
     "sptrsv_analyze": (c_int32, [c_int32, c_int64, c_void_p, c_void_p, c_void_p,
                                  c_void_p, POINTER(c_void_p)]),
+    "sptrsv_analyze_ex": (c_int32, [c_int32, c_int64, c_void_p, c_void_p, c_void_p,
+                                    c_int32, c_void_p, POINTER(c_void_p)]),
     "sptrsv_transform": (c_int32, [c_void_p, POINTER(TransformParams), c_void_p]),
     "sptrsv_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "sptrsv_check": (c_int32, [c_void_p, c_void_p]),
@@ -160,6 +163,14 @@ def sptrsv_analyze(n: int, nnz: int, d_row_ptr: int, d_col: int, d_val: int,
     out = c_void_p()
     _check(load().sptrsv_analyze(n, nnz, d_row_ptr, d_col, d_val, stream, byref(out)),
            "sptrsv_analyze")
+    return out.value
+
+
+def sptrsv_analyze_ex(n: int, nnz: int, d_row_ptr: int, d_col: int, d_val: int, op: int,
+                      stream: int = 0) -> int:
+    out = c_void_p()
+    _check(load().sptrsv_analyze_ex(n, nnz, d_row_ptr, d_col, d_val, op, stream, byref(out)),
+           "sptrsv_analyze_ex")
     return out.value
 
 
@@ -337,9 +348,10 @@ class Plan:
     """Owns an sptrsv plan built from a CSR matrix held in torch tensors.
 
     ``row_ptr``/``col`` int32 and ``val`` float64 CUDA tensors (or numpy
-    arrays, copied to the current device)."""
+    arrays, copied to the current device).  ``op`` (OP_*) names the system:
+    A x = b for a lower (default) or upper A, or A^T x = b."""
 
-    def __init__(self, n: int, row_ptr, col, val, stream=None):
+    def __init__(self, n: int, row_ptr, col, val, stream=None, op: int = OP_LOWER):
         import torch
         dev = torch.device("cuda", torch.cuda.current_device())
 
@@ -352,8 +364,9 @@ class Plan:
         rp, c, v = t(row_ptr, torch.int32), t(col, torch.int32), t(val, torch.float64)
         self.nnz = int(c.numel())
         self._handle = 0
-        self._handle = sptrsv_analyze(self.n, self.nnz, rp.data_ptr(), c.data_ptr(),
-                                      v.data_ptr(), _stream_handle(stream))
+        self.op = int(op)
+        self._handle = sptrsv_analyze_ex(self.n, self.nnz, rp.data_ptr(), c.data_ptr(),
+                                         v.data_ptr(), self.op, _stream_handle(stream))
 
     @property
     def handle(self) -> int:

@@ -415,6 +415,7 @@ sptrsv_status_t build_struct(sptrsv_plan_t p, SolveStruct<T> &ss, int L, cudaStr
                             ss.row_id.p, ss.diag.p, s));
     CK(ss.chunk_level.alloc(nchunks));
     CK(launch_chunk_level(nseg, ss.lvl_chunk.p, ss.chunk_level.p, s));
+    if (p->rev) CK(launch_struct_reverse(p->n, ss.row_id.p, total, ss.ecol.p, s));
     CK(cudaStreamSynchronize(s));
     ss.n = p->n;
     ss.nlev = nseg;
@@ -772,7 +773,7 @@ sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t 
     CKS(solve32(b, false));
     CK(launch_ir_update(x, p->d32.p, count, true, p->status.p, s));
     for (int it = 0; it < p->prm.ir_max_iter; ++it) {
-        CK(launch_residual(n, p->row_ptr.p, p->col.p, p->val.p, b, x, p->r64.p, nrhs, nrhs,
+        CK(launch_residual(n, p->row_ptr.p, p->col.p, p->val.p, p->rev, b, x, p->r64.p, nrhs, nrhs,
                            p->status.p, s));
         CK(launch_ir_decide(p->status.p, p->prm.ir_tol, p->lnorm.p, s));
         CKS(solve32(p->r64.p, true));
@@ -826,7 +827,14 @@ void sptrsv_default_params(sptrsv_transform_params_t *prm) {
 sptrsv_status_t sptrsv_analyze(int32_t n, int64_t nnz, const int32_t *d_row_ptr,
                                const int32_t *d_col, const double *d_val,
                                sptrsv_stream_t stream, sptrsv_plan_t *out) {
+    return sptrsv_analyze_ex(n, nnz, d_row_ptr, d_col, d_val, SPTRSV_OP_LOWER, stream, out);
+}
+
+sptrsv_status_t sptrsv_analyze_ex(int32_t n, int64_t nnz, const int32_t *d_row_ptr,
+                                  const int32_t *d_col, const double *d_val, int32_t op,
+                                  sptrsv_stream_t stream, sptrsv_plan_t *out) {
     if (!out) return SPTRSV_ERR_INVALID_ARG;
+    if (op < SPTRSV_OP_LOWER || op > SPTRSV_OP_UPPER_TRANS) return SPTRSV_ERR_INVALID_ARG;
     *out = nullptr;
     if (n < 0 || nnz < 0 || nnz > INT32_MAX) return SPTRSV_ERR_INVALID_ARG;
     if (n > 0 && (!d_row_ptr || (nnz > 0 && (!d_col || !d_val)))) return SPTRSV_ERR_INVALID_ARG;
@@ -851,6 +859,7 @@ sptrsv_status_t sptrsv_analyze(int32_t n, int64_t nnz, const int32_t *d_row_ptr,
     CKP(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
     p->n = n;
     p->nnz = nnz;
+    p->op = op;
     sptrsv_default_params(&p->prm);
     p->prm.select_mode = SPTRSV_SELECT_NONE;
     p->prm.solve_mode = SPTRSV_SOLVE_BARRIER;
@@ -878,9 +887,53 @@ sptrsv_status_t sptrsv_analyze(int32_t n, int64_t nnz, const int32_t *d_row_ptr,
         CKP(cudaMemcpyAsync(p->col.p, d_col, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
         CKP(cudaMemcpyAsync(p->val.p, d_val, nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
-    // validation
     DevArr<unsigned long long> err;
     CKP(err.alloc(1));
+    // other operators: bring op(A) to lower-triangular form (csrc/operator.cu)
+    if (op != SPTRSV_OP_LOWER) {
+        CKP(cudaMemsetAsync(err.p, 0xff, sizeof(unsigned long long), s));
+        CKP(launch_csr_check(n, nnz, p->row_ptr.p, p->col.p, err.p, s));
+        unsigned long long h_chk = 0;
+        CKP(cudaMemcpyAsync(&h_chk, err.p, sizeof(h_chk), cudaMemcpyDeviceToHost, s));
+        CKP(cudaStreamSynchronize(s));
+        if (h_chk != ~0ull) return fail((sptrsv_status_t)(h_chk & 0xff));
+        auto replace = [&](DevArr<int32_t> &rp, DevArr<int32_t> &cl, DevArr<double> &vl) {
+            p->row_ptr = std::move(rp);
+            p->col = std::move(cl);
+            p->val = std::move(vl);
+        };
+        if (op == SPTRSV_OP_LOWER_TRANS || op == SPTRSV_OP_UPPER_TRANS) {
+            DevArr<int32_t> trp, tcl, rows, order, cnt;
+            DevArr<double> tvl;
+            DevArr<int64_t> stmp0;
+            DevArr<char> rtmp;
+            CKP(trp.alloc((size_t)n + 1));
+            CKP(tcl.alloc(nnz));
+            CKP(tvl.alloc(nnz));
+            CKP(rows.alloc(nnz));
+            CKP(order.alloc(nnz));
+            CKP(cnt.alloc(n));
+            CKP(stmp0.alloc(scan_tmp_elems(n)));
+            CKP(rtmp.alloc(radix_tmp_bytes((int32_t)nnz)));
+            CKP(launch_csr_transpose(n, nnz, p->row_ptr.p, p->col.p, p->val.p, trp.p, tcl.p,
+                                     tvl.p, rows.p, order.p, cnt.p, stmp0.p, rtmp.p, s));
+            CKP(cudaStreamSynchronize(s));
+            replace(trp, tcl, tvl);
+        }
+        if (op == SPTRSV_OP_UPPER || op == SPTRSV_OP_LOWER_TRANS) {
+            DevArr<int32_t> rrp, rcl;
+            DevArr<double> rvl;
+            CKP(rrp.alloc((size_t)n + 1));
+            CKP(rcl.alloc(nnz));
+            CKP(rvl.alloc(nnz));
+            CKP(launch_csr_reverse(n, nnz, p->row_ptr.p, p->col.p, p->val.p, rrp.p, rcl.p,
+                                   rvl.p, s));
+            CKP(cudaStreamSynchronize(s));
+            replace(rrp, rcl, rvl);
+            p->rev = true;
+        }
+    }
+    // validation
     CKP(cudaMemsetAsync(err.p, 0xff, sizeof(unsigned long long), s));
     CKP(p->offdeg.alloc(n));
     CKP(launch_validate(n, nnz, p->row_ptr.p, p->col.p, p->val.p, p->offdeg.p, err.p,
@@ -1062,6 +1115,7 @@ sptrsv_status_t sptrsv_get_info(sptrsv_plan_t p, sptrsv_info_t *o) {
     o->chosen_depth = p->chosen_depth;
     o->analyze_ms = p->analyze_ms;
     o->transform_ms = p->transform_ms;
+    o->op = p->op;
     if (p->status.p) {
         DevStatus h;
         if (cudaMemcpy(&h, p->status.p, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess)
@@ -1092,6 +1146,7 @@ sptrsv_status_t sptrsv_get_levels(sptrsv_plan_t p, int32_t *d_level, int32_t *d_
                            cudaMemcpyDeviceToDevice, s));
     if (d_perm)
         CK(cudaMemcpyAsync(d_perm, p->perm.p, p->n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    if (p->rev) CK(launch_levels_reverse(p->n, d_level, d_perm, s));
     CK(cudaStreamSynchronize(s));
     return SPTRSV_OK;
 }

@@ -187,6 +187,7 @@ SPTRSV_API sptrsv_status_t sptrsv_batch_solve(sptrsv_batch_t bt, const double *c
         M.row_ptr = p->row_ptr.p;
         M.col = p->col.p;
         M.val = p->val.p;
+        M.rev = p->rev ? 1 : 0;
         M.b = d_b[i];
         M.x = d_x[i];
         M.d32 = bt->ir ? bt->d32.p + off[i] : nullptr;

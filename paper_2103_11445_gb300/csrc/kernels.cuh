@@ -51,4 +51,29 @@ size_t radix_tmp_bytes(int32_t n);
 cudaError_t launch_level_perm(int32_t n, const int32_t *level, int32_t nlev,
                               int32_t *perm, void *tmp, cudaStream_t s);
 
+// ---- operator.cu ----------------------------------------------------------
+// Structural check before a transpose: row_ptr monotone inside [0, nnz],
+// columns in [0, n).  err as for launch_validate.
+cudaError_t launch_csr_check(int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col,
+                             unsigned long long *err, cudaStream_t s);
+// B = P A P, P the exchange permutation (turns an upper triangle into a lower
+// one and back).
+cudaError_t launch_csr_reverse(int32_t n, int64_t nnz, const int32_t *rp, const int32_t *col,
+                               const double *val, int32_t *orp, int32_t *ocol, double *oval,
+                               cudaStream_t s);
+// B = A^T with ascending columns in every row.  Scratch: rows[nnz],
+// order[nnz], cnt[n], scan_tmp[scan_tmp_elems(n)], radix_tmp of
+// radix_tmp_bytes(nnz) bytes.
+cudaError_t launch_csr_transpose(int32_t n, int64_t nnz, const int32_t *rp, const int32_t *col,
+                                 const double *val, int32_t *orp, int32_t *ocol, double *oval,
+                                 int32_t *rows, int32_t *order, int32_t *cnt, int64_t *scan_tmp,
+                                 void *radix_tmp, cudaStream_t s);
+// Solve structure built on P A P -> the caller's numbering (row ids, x and b
+// columns mirrored; pads and run slots kept).
+cudaError_t launch_struct_reverse(int32_t n, int32_t *row_id, int64_t count, int32_t *ecol,
+                                  cudaStream_t s);
+// Level export of a mirrored plan in the caller's rows: level[] reversed,
+// perm[] entries mirrored (either may be null).
+cudaError_t launch_levels_reverse(int32_t n, int32_t *level, int32_t *perm, cudaStream_t s);
+
 }  // namespace sptrsv

@@ -104,7 +104,7 @@ extern "C" SPTRSV_API sptrsv_status_t sptrsv_solve_ir_noalloc(sptrsv_plan_t p, c
     if ((e = launch_ir_update(d_x, d32, count, true, p->status.p, s)) != cudaSuccess)
         return to_status(e);
     for (int it = 0; it < p->prm.ir_max_iter; ++it) {
-        if ((e = launch_residual(n, p->row_ptr.p, p->col.p, p->val.p, d_b, d_x, r64, nrhs, nrhs,
+        if ((e = launch_residual(n, p->row_ptr.p, p->col.p, p->val.p, p->rev, d_b, d_x, r64, nrhs, nrhs,
                                  p->status.p, s)) != cudaSuccess)
             return to_status(e);
         if ((e = launch_ir_decide(p->status.p, p->prm.ir_tol, p->lnorm.p, s)) != cudaSuccess)

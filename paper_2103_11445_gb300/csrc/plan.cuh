@@ -97,7 +97,10 @@ struct sptrsv_plan_s {
     int num_sms = 0;
     int32_t n = 0;
     int64_t nnz = 0;
-    sptrsv::DevArr<int32_t> row_ptr, col;
+    int32_t op = 0;              // SPTRSV_OP_* the caller asked for
+    bool rev = false;            // row_ptr/col/val hold P A P (A upper): the
+                                 // solve structure is mirrored back to A's numbering
+    sptrsv::DevArr<int32_t> row_ptr, col;   // the lower-triangular operator analysed
     sptrsv::DevArr<double> val;
     sptrsv::DevArr<int32_t> offdeg, level, level_ptr, perm;
     std::vector<int32_t> h_level_ptr;

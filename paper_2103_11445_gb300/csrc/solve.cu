@@ -593,22 +593,29 @@ const void *pick_kernel(int L, int nr, bool syncfree) {
 // ---------------------------------------------------------------------------
 // Refinement kernels (FP64 residual of the original L, FP32 corrections).
 
+// r = b - A x with A the caller's operator.  The CSR holds the lower
+// triangle the plan analysed; with rev it is P A P, so its row i is A's row
+// n-1-i and its column c is A's column n-1-c.
 __global__ void residual_kernel(int32_t n, const int32_t *__restrict__ row_ptr,
                                 const int32_t *__restrict__ col,
-                                const double *__restrict__ val, const double *__restrict__ b,
-                                const double *__restrict__ x, double *__restrict__ r, int nr,
-                                int ld, DevStatus *st) {
+                                const double *__restrict__ val, int rev,
+                                const double *__restrict__ b, const double *__restrict__ x,
+                                double *__restrict__ r, int nr, int ld, DevStatus *st) {
     if (converged(st)) return;
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     double rmax = 0.0, xmax = 0.0;
     if (i < n) {
         const int32_t a = row_ptr[i], e = row_ptr[i + 1];
+        const int64_t ri = rev ? n - 1 - i : i;
         for (int c = 0; c < nr; ++c) {
-            double s = b[(int64_t)i * ld + c];
-            for (int32_t k = a; k < e; ++k) s -= val[k] * x[(int64_t)col[k] * ld + c];
-            r[(int64_t)i * ld + c] = s;
+            double s = b[ri * ld + c];
+            for (int32_t k = a; k < e; ++k) {
+                const int64_t j = rev ? n - 1 - col[k] : col[k];
+                s -= val[k] * x[j * ld + c];
+            }
+            r[ri * ld + c] = s;
             rmax = fmax(rmax, fabs(s));
-            xmax = fmax(xmax, fabs(x[(int64_t)i * ld + c]));
+            xmax = fmax(xmax, fabs(x[ri * ld + c]));
         }
     }
 #pragma unroll
@@ -773,13 +780,16 @@ batch_kernel(const BatchMat *__restrict__ mats, int32_t nmats, BatchCtl *ctl, De
         double rmax = 0.0, xmax = 0.0;
         for (int64_t row = gt; row < (int64_t)M.n; row += gthreads) {
             const int32_t a = M.row_ptr[row], e = M.row_ptr[row + 1];
+            const int64_t ri = M.rev ? M.n - 1 - row : row;  // see residual_kernel
             for (int c = 0; c < M.nr; ++c) {
-                double s = M.b[row * M.nr + c];
-                for (int32_t k = a; k < e; ++k)
-                    s -= M.val[k] * __ldcg(M.x + (int64_t)M.col[k] * M.nr + c);
-                M.r64[row * M.nr + c] = s;
+                double s = M.b[ri * M.nr + c];
+                for (int32_t k = a; k < e; ++k) {
+                    const int64_t j = M.rev ? M.n - 1 - M.col[k] : M.col[k];
+                    s -= M.val[k] * __ldcg(M.x + j * M.nr + c);
+                }
+                M.r64[ri * M.nr + c] = s;
                 rmax = fmax(rmax, fabs(s));
-                xmax = fmax(xmax, fabs(__ldcg(M.x + row * M.nr + c)));
+                xmax = fmax(xmax, fabs(__ldcg(M.x + ri * M.nr + c)));
             }
         }
         atomic_max_abs(&C->norms[it][0], rmax);
@@ -896,10 +906,11 @@ template cudaError_t launch_solve<float>(const SolveData<float> &, const double 
                                          DevStatus *, uint64_t, bool, cudaStream_t);
 
 cudaError_t launch_residual(int32_t n, const int32_t *row_ptr, const int32_t *col,
-                            const double *val, const double *b, const double *x, double *r,
-                            int nr, int ld, DevStatus *st, cudaStream_t s) {
+                            const double *val, bool rev, const double *b, const double *x,
+                            double *r, int nr, int ld, DevStatus *st, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    residual_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, row_ptr, col, val, b, x, r, nr, ld, st);
+    residual_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, row_ptr, col, val, rev ? 1 : 0, b, x, r,
+                                                    nr, ld, st);
     return cudaGetLastError();
 }
 

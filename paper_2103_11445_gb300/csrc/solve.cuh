@@ -67,9 +67,10 @@ constexpr int kBatchMaxIter = 16;
 struct BatchMat {
     SolveData<float> s32;     // FP32 structure (refinement)
     SolveData<double> s64;    // FP64 structure (direct solve)
-    const int32_t *row_ptr;   // original L for the FP64 residual
+    const int32_t *row_ptr;   // the analysed lower triangle, for the FP64 residual
     const int32_t *col;
     const double *val;
+    int32_t rev;              // the CSR is P A P (see residual_kernel)
     const double *b;          // [n, nr] row-major
     double *x;
     float *d32;               // scratch [n, nr]
@@ -95,9 +96,10 @@ int batch_max_coresident(bool ir, int block_threads, int num_sms);
 
 // FP64 residual r = b - L x over the original CSR, with infinity norms of r
 // and x accumulated in st->norms[0], [1]; returns at once when ir_flag is set.
+// r = b - A x; rev: the CSR holds P A P (see residual_kernel).
 cudaError_t launch_residual(int32_t n, const int32_t *row_ptr, const int32_t *col,
-                            const double *val, const double *b, const double *x, double *r,
-                            int nr, int ld, DevStatus *st, cudaStream_t s);
+                            const double *val, bool rev, const double *b, const double *x,
+                            double *r, int nr, int ld, DevStatus *st, cudaStream_t s);
 // Refinement bookkeeping.
 cudaError_t launch_ir_begin(DevStatus *st, const double *b, int64_t count, cudaStream_t s);
 cudaError_t launch_ir_decide(DevStatus *st, double tol, const unsigned long long *lnorm,
