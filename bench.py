@@ -262,6 +262,9 @@ def select_kw(name: str, Bd) -> dict:
         return dict(select_mode=Bd.SELECT_NONE)
     if name == "heuristic":
         return dict(select_mode=Bd.SELECT_HEURISTIC)
+    if name == "heuristic_thin32_d16":
+        return dict(select_mode=Bd.SELECT_HEURISTIC, thin_rows=32, max_depth=16,
+                    flop_budget=4.0)
     if name.startswith("fixed_d"):
         return dict(select_mode=Bd.SELECT_FIXED, depth=int(name[len("fixed_d"):]))
     raise ValueError(name)
@@ -346,7 +349,10 @@ def run_ours(args, world, rank, local):
 
     # candidates: plain level sets, heuristic H, fixed depths; each autotuned
     cands = [("plain", dict(select_mode=Bd.SELECT_NONE)),
-             ("heuristic", dict(select_mode=Bd.SELECT_HEURISTIC))]
+             ("heuristic", dict(select_mode=Bd.SELECT_HEURISTIC)),
+             # H restricted to levels narrower than one warp, deep, 4x FLOP budget
+             ("heuristic_thin32_d16", dict(select_mode=Bd.SELECT_HEURISTIC, thin_rows=32,
+                                           max_depth=16, flop_budget=4.0))]
     for d in [int(v) for v in args.depths.split(",") if v.strip()]:
         cands.append((f"fixed_d{d}", dict(select_mode=Bd.SELECT_FIXED, depth=d)))
     results = {}

@@ -137,7 +137,7 @@ typedef struct {
                                 (valid after a synchronisation) */
     int32_t num_sms;
     int32_t poll_backoff_ns;
-    int32_t chosen_depth;    /* SELECT_COSTMODEL: depth the network picked
+    int32_t chosen_depth;    /* SELECT_COSTMODEL: candidate code the network picked
                                 (-1 when it did not run) */
     double analyze_ms, transform_ms;
     int32_t op;              /* SPTRSV_OP_* of the plan */
@@ -233,17 +233,23 @@ SPTRSV_API sptrsv_status_t sptrsv_get_transformed(sptrsv_plan_t p, int32_t *d_ne
 /* ---- Learned cost model ----------------------------------------------
  * The paper picks the rows to rewrite by hand (Sec. IV).  With a network
  * attached (sptrsv_set_costmodel), SPTRSV_SELECT_COSTMODEL predicts the log
- * solve time of merging every d+1 levels for d in {0,1,2,3,4,6,8} from 16
- * features per candidate and keeps the argmin; without one it falls back to
- * heuristic H.  The network: F -> H -> H -> 1, ReLU, FP32, weights in one
+ * solve time of every candidate rewrite from 17 features per candidate and
+ * keeps the argmin; without one it falls back to heuristic H.  Candidates
+ * (codes): d in {0,1,2,3,4,6,8} merges every d+1 levels (0 = plain level
+ * sets); 100 + d in {108, 116} rewrites only the levels of fewer than 32
+ * rows, up to d of them into the level before, within 4x the plain FLOPs
+ * (heuristic H with those parameters).  sptrsv_info_t.chosen_depth is the
+ * chosen code.  The network: F -> H -> H -> 1, ReLU, FP32, weights in one
  * flat array W1[F][H], b1[H], W2[H][H], b2[H], W3[H], b3 (row-major). */
 
-/* Features of the candidate depths (h_feat: [nd][16] floats, host):
+/* Features of candidate codes (h_feat: [nd][17] floats, host; a code is
+ * d in 0..16 or 100 + d with d in 0..16, SPTRSV_ERR_INVALID_ARG otherwise):
  *  0 log2 n, 1 log2 nnz, 2 dependencies per row, 3 log2 levels,
  *  4 log2 rows per level, 5-6 fraction of levels with < 32 / < 1024 rows,
  *  7 fraction of rows in levels of < 1024 rows, 8-11 fraction of rows with
  *  0 | 1-2 | 3-6 | >= 7 dependencies, 12 d, 13 log2 levels after merging,
- *  14 FLOPs after / FLOPs before, 15 fraction of rows rewritten.
+ *  14 FLOPs after / FLOPs before, 15 fraction of rows rewritten, 16 1 for a
+ *  thin-levels-only candidate, else 0.
  * Fill counts come from the device rewriting kernels; synchronises. */
 SPTRSV_API sptrsv_status_t sptrsv_costmodel_features(sptrsv_plan_t p, const int32_t *h_depths,
                                                      int32_t nd, float *h_feat,

@@ -238,10 +238,13 @@ def sptrsv_last_kernel_ms(plan: int) -> float:
     return float(ms.value)
 
 
-def sptrsv_costmodel_features(plan: int, depths, stream: int = 0):
+COSTMODEL_FEATURES = 17
+
+
+def sptrsv_costmodel_features(plan: int, codes, stream: int = 0):
     import numpy as np
-    d = np.ascontiguousarray(depths, dtype=np.int32)
-    out = np.zeros((d.size, 16), dtype=np.float32)
+    d = np.ascontiguousarray(codes, dtype=np.int32)
+    out = np.zeros((d.size, COSTMODEL_FEATURES), dtype=np.float32)
     _check(load().sptrsv_costmodel_features(plan, d.ctypes.data, d.size, out.ctypes.data,
                                             stream), "sptrsv_costmodel_features")
     return out

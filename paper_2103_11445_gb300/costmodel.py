@@ -1,9 +1,11 @@
 """Learned choice of the rewriting depth.
 
 The paper chooses the rows to rewrite by hand (Sec. IV).  Here a small network
-(``libsptrsv`` cost-model kernels: 16 features -> 64 -> 64 -> 1, ReLU, FP32,
-trained with Adam on the GPU) predicts the log solve time of "merge every
-d+1 levels" for d in DEPTHS, and ``SPTRSV_SELECT_COSTMODEL`` keeps the argmin.
+(``libsptrsv`` cost-model kernels: 17 features -> 64 -> 64 -> 1, ReLU, FP32,
+trained with Adam on the GPU) predicts the log solve time of every candidate
+in CANDIDATES -- "merge every d+1 levels" (code d) or "rewrite only the levels
+under 32 rows, up to d deep" (code 100 + d) -- and
+``SPTRSV_SELECT_COSTMODEL`` keeps the argmin.
 Heuristic H remains the fallback when no network is attached, and the
 baseline the network is judged against.
 
@@ -27,8 +29,11 @@ import numpy as np
 
 from . import binding as B
 
-DEPTHS = (0, 1, 2, 3, 4, 6, 8)
-N_FEATURES = 16
+CANDIDATES = (0, 1, 2, 3, 4, 6, 8, 108, 116)
+THIN_ONLY = 100      # code 100 + d: levels under THIN_ROWS rows only, depth <= d
+THIN_ROWS = 32
+THIN_BUDGET = 4.0
+N_FEATURES = 17
 HIDDEN = 64
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "costmodel_weights.npz")
 # launch shape used for the timing labels and for the model's own plans
@@ -98,7 +103,7 @@ class CostModel:
     # -- persistence ------------------------------------------------------------
     def save(self, path: str = WEIGHTS) -> None:
         np.savez(path, params=self.params(), mean=self.mean, std=self.std,
-                 n_in=self.n_in, hidden=self.hidden, depths=np.array(DEPTHS))
+                 n_in=self.n_in, hidden=self.hidden, candidates=np.array(CANDIDATES))
 
     @classmethod
     def load(cls, path: str = WEIGHTS) -> "CostModel":
@@ -143,18 +148,26 @@ def heuristic_time(plan: "B.Plan", n: int, reps: int = 5) -> float:
     return time_solves(plan, n, reps)
 
 
+def candidate_kw(code: int) -> dict:
+    """Transform parameters that realise a candidate code."""
+    if code >= THIN_ONLY:
+        return dict(select_mode=B.SELECT_HEURISTIC, thin_rows=THIN_ROWS,
+                    max_depth=code - THIN_ONLY, flop_budget=THIN_BUDGET)
+    if code == 0:
+        return dict(select_mode=B.SELECT_NONE)
+    return dict(select_mode=B.SELECT_FIXED, depth=code)
+
+
 def collect(specs, reps: int = 5, with_heuristic: bool = True, log=None):
-    """Features and measured log2 times (us) for every spec and depth."""
+    """Features and measured log2 times (us) for every spec and candidate."""
     import matgen as mg
     X, y, group, hs = [], [], [], []
     for k, sp in enumerate(specs):
         A = mg.make_from_spec(sp)
         P = B.Plan(A.n, A.row_ptr, A.col, A.val)
-        feats = B.sptrsv_costmodel_features(P.handle, DEPTHS)
-        for d, f in zip(DEPTHS, feats):
-            kw = dict(select_mode=B.SELECT_FIXED, depth=d) if d else \
-                dict(select_mode=B.SELECT_NONE)
-            P.transform(**kw, **LABEL_LAUNCH)
+        feats = B.sptrsv_costmodel_features(P.handle, CANDIDATES)
+        for code, f in zip(CANDIDATES, feats):
+            P.transform(**candidate_kw(code), **LABEL_LAUNCH)
             us = time_solves(P, A.n, reps)
             X.append(f)
             y.append(np.log2(us))
@@ -211,7 +224,7 @@ def main(argv=None) -> int:
                                nrhs_max=1, band_range=(5, 20))
         t0 = time.time()
         X, y, g, h = collect(specs, reps=args.reps, log=lambda s: print(s, flush=True))
-        np.savez(args.out, X=X, y=y, group=g, h=h, depths=np.array(DEPTHS),
+        np.savez(args.out, X=X, y=y, group=g, h=h, candidates=np.array(CANDIDATES),
                  specs=np.array([str(s) for s in specs]))
         print(f"collected {len(specs)} matrices in {time.time() - t0:.1f} s")
         return 0

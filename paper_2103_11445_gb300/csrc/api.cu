@@ -209,9 +209,16 @@ sptrsv_status_t compute_segments(sptrsv_plan_t p, int64_t tau, int32_t d_max, do
 }
 
 // Candidate rewrite depths the cost model chooses from (0 = plain levels).
-constexpr int kCostDepths[] = {0, 1, 2, 3, 4, 6, 8};
-constexpr int kNumCostDepths = 7;
-constexpr int kCostFeatures = 16;
+// Candidates of SELECT_COSTMODEL.  A code c < kThinOnly merges every c+1
+// levels (c = 0: the plain level sets); c = kThinOnly + d rewrites only the
+// levels of fewer than kThinRows rows (one warp), up to d of them into the
+// level before, within kThinBudget times the plain FLOPs.
+constexpr int kThinOnly = 100;
+constexpr int kThinRows = 32;
+constexpr double kThinBudget = 4.0;
+constexpr int kCostDepths[] = {0, 1, 2, 3, 4, 6, 8, kThinOnly + 8, kThinOnly + 16};
+constexpr int kNumCostDepths = 9;
+constexpr int kCostFeatures = 17;
 
 // Features of "merge every d+1 levels" on this plan (the analysis features
 // of the matrix-analysis module, Sec. IV, plus the candidate's fill):
@@ -220,7 +227,9 @@ constexpr int kCostFeatures = 16;
 //  7 fraction of rows in levels of < 1024 rows, 8-11 fraction of rows with
 //  0 | 1-2 | 3-6 | >= 7 dependencies, 12 d, 13 log2 levels after,
 //  14 FLOPs after / FLOPs before, 15 fraction of rows rewritten.
-sptrsv_status_t candidate_features(sptrsv_plan_t p, int d, float *f, cudaStream_t s) {
+sptrsv_status_t candidate_features(sptrsv_plan_t p, int code, float *f, cudaStream_t s) {
+    const bool thin_only = code >= kThinOnly;
+    const int d = thin_only ? code - kThinOnly : code;
     const double n = std::max<int32_t>(p->n, 1), nnz = std::max<int64_t>(p->nnz, 1);
     const int32_t nlev = std::max<int32_t>(p->nlev, 1);
     int64_t thin32 = 0, thin1k = 0, rows1k = 0;
@@ -233,7 +242,8 @@ sptrsv_status_t candidate_features(sptrsv_plan_t p, int d, float *f, cudaStream_
     std::vector<std::pair<int32_t, int32_t>> segs;
     int64_t added = 0;
     if (d > 0 && p->nlev > 0) {
-        CKS(compute_segments(p, INT64_MAX, d, INFINITY, s, &segs, &added));
+        if (thin_only) CKS(compute_segments(p, kThinRows, d, kThinBudget, s, &segs, &added));
+        else CKS(compute_segments(p, INT64_MAX, d, INFINITY, s, &segs, &added));
     } else {
         for (int32_t l = 0; l < p->nlev; ++l) segs.emplace_back(l, 0);
     }
@@ -254,6 +264,7 @@ sptrsv_status_t candidate_features(sptrsv_plan_t p, int d, float *f, cudaStream_
     f[13] = (float)std::log2((double)std::max<size_t>(segs.size(), 1));
     f[14] = (float)((fp + added) / fp);
     f[15] = (float)(rewritten / n);
+    f[16] = thin_only ? 1.0f : 0.0f;
     return SPTRSV_OK;
 }
 
@@ -284,9 +295,15 @@ sptrsv_status_t choose_segments(sptrsv_plan_t p, cudaStream_t s) {
         for (int i = 1; i < kNumCostDepths; ++i)
             if (pred[i] < pred[best]) best = i;
         p->chosen_depth = kCostDepths[best];
-        tau = INT64_MAX;
-        d_max = kCostDepths[best];
-        rho = INFINITY;
+        if (kCostDepths[best] >= kThinOnly) {
+            tau = kThinRows;
+            d_max = kCostDepths[best] - kThinOnly;
+            rho = kThinBudget;
+        } else {
+            tau = INT64_MAX;
+            d_max = kCostDepths[best];
+            rho = INFINITY;
+        }
     } else if (prm.select_mode == SPTRSV_SELECT_FIXED) {
         tau = INT64_MAX;
         d_max = prm.depth;
@@ -1205,7 +1222,9 @@ sptrsv_status_t sptrsv_costmodel_features(sptrsv_plan_t p, const int32_t *h_dept
     if (!p || nd < 0 || (nd > 0 && (!h_depths || !h_feat))) return SPTRSV_ERR_INVALID_ARG;
     if (p->latched != SPTRSV_OK) return SPTRSV_ERR_BAD_STATE;
     for (int32_t i = 0; i < nd; ++i) {
-        if (h_depths[i] < 0 || h_depths[i] > 16) return SPTRSV_ERR_INVALID_ARG;
+        const int32_t c = h_depths[i];
+        if (c < 0 || (c > 16 && c < kThinOnly) || c > kThinOnly + 16)
+            return SPTRSV_ERR_INVALID_ARG;
         CKS(candidate_features(p, h_depths[i], h_feat + (int64_t)i * kCostFeatures,
                                (cudaStream_t)stream));
     }

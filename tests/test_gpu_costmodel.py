@@ -13,7 +13,7 @@ from oracle import rewrite as rw
 
 pytestmark = pytest.mark.gpu
 
-F, H = 16, 64
+F, H = 17, 64
 
 
 def oracle_params(flat, n_in=F, hidden=H):
@@ -103,22 +103,26 @@ def test_training_fits_a_smooth_target():
     net.close()
 
 
-@pytest.mark.parametrize("d", [0, 1, 3, 8])
-def test_features_match_oracle_transform(d):
+@pytest.mark.parametrize("code", [0, 1, 3, 8, 108, 116])
+def test_features_match_oracle_transform(code):
     from paper_2103_11445_gb300 import binding as B
     A = mg.thin_tail(20_000, seed=3000)
     P = B.Plan(A.n, A.row_ptr, A.col, A.val)
-    f = B.sptrsv_costmodel_features(P.handle, [d])[0]
+    f = B.sptrsv_costmodel_features(P.handle, [code])[0]
     lv, nl = oracle.levels(A)
+    thin = code >= 100
+    d = code - 100 if thin else code
     if d:
-        tr = rw.transform(A, lv, nl, tau=10**12, d_max=d, rho=float("inf"), max_fill=1024)
+        tau, rho = (32, 4.0) if thin else (10**12, float("inf"))
+        tr = rw.transform(A, lv, nl, tau=tau, d_max=d, rho=rho, max_fill=1024)
         nnew, added, rewritten = tr.nlev_new, tr.added_flops, len(tr.rows)
     else:
         nnew, added, rewritten = nl, 0, 0
     sizes = np.bincount(lv)
     offd = np.diff(A.row_ptr) - 1
     assert np.isclose(f[0], np.log2(A.n), rtol=1e-6) and np.isclose(f[3], np.log2(nl), rtol=1e-6)
-    assert f[12] == d and np.isclose(f[13], np.log2(nnew), rtol=1e-6)
+    assert f[12] == d and f[16] == (1.0 if thin else 0.0)
+    assert np.isclose(f[13], np.log2(nnew), rtol=1e-6)
     assert np.isclose(f[14], (rw.total_flops(A) + added) / rw.total_flops(A), rtol=1e-6)
     assert np.isclose(f[15], rewritten / A.n, rtol=1e-6)
     assert np.isclose(f[5], (sizes < 32).mean(), rtol=1e-6)
@@ -128,10 +132,12 @@ def test_features_match_oracle_transform(d):
     P.close()
 
 
-@pytest.mark.parametrize("sign,expect", [(1.0, 0), (-1.0, 8)])
+@pytest.mark.parametrize("sign,expect", [(1.0, 0), (-1.0, 116)])
 def test_costmodel_selection_takes_the_argmin(sign, expect):
-    """A hand-built network whose output is +d or -d must make the plan pick
-    depth 0 or 8; the solve must still match the oracle."""
+    """A hand-built network whose output is +d or -d (d = feature 12) must
+    make the plan pick the plain level sets (code 0) or the deepest candidate
+    (thin levels only, depth 16: code 116); the solve must still match the
+    oracle."""
     from paper_2103_11445_gb300 import binding as B
     from paper_2103_11445_gb300 import costmodel as cm
     params = np.zeros(B.sptrsv_mlp_num_params(F, H), np.float32)
@@ -145,8 +151,10 @@ def test_costmodel_selection_takes_the_argmin(sign, expect):
     P.transform(select_mode=B.SELECT_COSTMODEL, solve_mode=B.SOLVE_SYNCFREE)
     info = P.info()
     assert info["chosen_depth"] == expect
-    if expect:
-        assert info["nlev_new"] == -(-info["nlev"] // (expect + 1))
+    if expect:   # stencil2d(32): levels under 32 rows are the 31 + 31 corner levels
+        lv, nl = oracle.levels(A)
+        tr = rw.transform(A, lv, nl, tau=32, d_max=16, rho=4.0, max_fill=1024)
+        assert info["nlev_new"] == tr.nlev_new < info["nlev"]
     b = mg.rhs_uniform(A.n, seed=2)
     import torch
     x = P.solve(torch.as_tensor(b, device="cuda"))
