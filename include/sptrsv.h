@@ -147,8 +147,10 @@ SPTRSV_API const char *sptrsv_status_string(sptrsv_status_t s);
 SPTRSV_API void sptrsv_default_params(sptrsv_transform_params_t *prm);
 
 /* Level analysis of DAG_L (Sec. II; level sets as in Sec. II's related
- * work, built here on the device by validation, a transpose and a parallel
- * breadth-first traversal of the DAG, Sec. IV's matrix-analysis module).
+ * work, built here on the device by validation and a synchronisation-free
+ * pass over the rows in order -- each row's level is one more than the
+ * deepest of its dependencies -- then a stable sort of the rows by level;
+ * Sec. IV's matrix-analysis module).
  * Copies the CSR into the plan, so the caller may free it afterwards.
  * Returns the validation error codes above for malformed CSR.  On success
  * *out is a plan that solves the plain level sets. */

@@ -1,9 +1,7 @@
 // Matrix analysis on the device (the paper's matrix-analysis module, Sec. IV):
-// CSR validation, the successor lists of DAG_L (Sec. II), the level of every
-// row by a breadth-first (Kahn) traversal of DAG_L, and the level-ordered
-// row permutation by a stable radix sort.
-#include <cooperative_groups.h>
-
+// CSR validation, the level of every row of DAG_L (Sec. II) by a
+// synchronisation-free pass in row order, and the level-ordered row
+// permutation by a stable radix sort.
 #include "kernels.cuh"
 
 namespace sptrsv {
@@ -49,82 +47,77 @@ __global__ void validate_kernel(int32_t n, int64_t nnz, const int32_t *__restric
     if (code) atomicMin(err, ((unsigned long long)i << 8) | (unsigned long long)code);
 }
 
-__global__ void count_succ_kernel(int32_t n, const int32_t *__restrict__ row_ptr,
-                                  const int32_t *__restrict__ col, int32_t *tcnt) {
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    for (int32_t k = row_ptr[i]; k < row_ptr[i + 1] - 1; ++k) atomicAdd(&tcnt[col[k]], 1);
-}
-
-__global__ void fill_succ_kernel(int32_t n, const int32_t *__restrict__ row_ptr,
-                                 const int32_t *__restrict__ col,
-                                 const int32_t *__restrict__ tptr, int32_t *tcur,
-                                 int32_t *tidx) {
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    for (int32_t k = row_ptr[i]; k < row_ptr[i + 1] - 1; ++k) {
-        const int32_t j = col[k];
-        tidx[tptr[j] + atomicAdd(&tcur[j], 1)] = i;
-    }
-}
-
 // ---------------------------------------------------------------------------
-// Breadth-first level analysis in one cooperative launch.  Round m expands
-// the frontier of level m (queue[lo, hi)): every successor whose remaining
-// in-degree drops to zero joins level m+1 and is appended behind hi through
-// counter cnt3[(m+1) % 3].  After the grid barrier every CTA reads that
-// counter to learn the next frontier.  Three counters rotate so that a
-// counter is reset (during round m, for use in round m+2... i.e. the one
-// last read before the previous barrier) while nobody reads or appends it.
-constexpr int kBfsThreads = 512;
+// Level analysis without a barrier per level: level[i] = 0 for a row without
+// dependencies, else 1 + the largest level among them (Sec. II), computed in
+// row order by a persistent, co-resident grid.  Warp w takes rows w, w + nw,
+// ... ; its lanes split the row's dependencies, poll (bounded) each one's
+// level until it is set (levels start at -1) and reduce the maximum.  The
+// lowest unfinished row's warp has finished its earlier rows and the row's
+// dependencies all lie below it, so some warp can always make progress.
+// The critical path is one poll hop per level instead of a grid barrier.
+constexpr int kLevThreads = 256;
 
-__global__ void __launch_bounds__(kBfsThreads)
-bfs_levels_kernel(int32_t n, const int32_t *__restrict__ tptr,
-                  const int32_t *__restrict__ tidx, int32_t *indeg, int32_t *level,
-                  int32_t *queue, int32_t *cnt3, int32_t *level_start,
-                  int32_t *nlev_out, DevStatus *st, uint64_t timeout_ns) {
-    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
-    unsigned long long bar = 0;
-    // level 0: rows without dependencies
-    for (int64_t i = gtid; i < n; i += gthreads) {
-        if (indeg[i] == 0) {
-            level[i] = 0;
-            queue[atomicAdd(&cnt3[0], 1)] = (int32_t)i;
-        }
-    }
-    bool ok = grid_barrier(st, (++bar) * gridDim.x, timeout_ns, -1);
-    int32_t lo = 0;
-    int32_t hi = ok ? (int32_t)ld_relaxed_u32(&cnt3[0]) : 0;
-    int32_t m = 0;
-    while (ok && hi > lo) {
-        if (gtid == 0) {
-            level_start[m] = lo;
-            cnt3[(m + 2) % 3] = 0;  // last read before the previous barrier
-        }
-        int32_t *next_cnt = &cnt3[(m + 1) % 3];
-        for (int64_t q = lo + gtid; q < hi; q += gthreads) {
-            const int32_t r = __ldcg(&queue[q]);
-            const int32_t e = tptr[r + 1];
-            for (int32_t k = tptr[r]; k < e; ++k) {
-                const int32_t s = tidx[k];
-                if (atomicSub(&indeg[s], 1) == 1) {
-                    level[s] = m + 1;
-                    queue[hi + atomicAdd(next_cnt, 1)] = s;
-                }
+__device__ __forceinline__ int32_t ld_volatile_i32(const int32_t *p) {
+    int32_t v;
+    asm volatile("ld.volatile.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __noinline__ int32_t wait_level(const int32_t *p, DevStatus *st, uint64_t timeout_ns) {
+    WaitBudget wb(timeout_ns);
+    unsigned it = 0;
+    int32_t v;
+    do {
+        if ((++it & kPollMask) == 0 && wb.expired(st, -6)) return -1;
+        v = ld_volatile_i32(p);
+    } while (v < 0);
+    return v;
+}
+
+__global__ void __launch_bounds__(kLevThreads)
+levels_syncfree_kernel(int32_t n, const int32_t *__restrict__ row_ptr,
+                       const int32_t *__restrict__ col, int32_t *level, int32_t *nlev_out,
+                       DevStatus *st, uint64_t timeout_ns) {
+    const int lane = threadIdx.x & 31;
+    const int32_t gw = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int32_t nw = (int32_t)((gridDim.x * blockDim.x) >> 5);
+    int32_t deepest = -1;
+    for (int32_t i = gw; i < n; i += nw) {
+        const int32_t a = __ldg(row_ptr + i), e = __ldg(row_ptr + i + 1) - 1;  // diagonal last
+        int32_t m = -1;
+        bool bail = false;
+        for (int32_t k = a + lane; k < e; k += 32) {
+            const int32_t *pj = level + __ldg(col + k);
+            int32_t v = ld_volatile_i32(pj);
+            if (v < 0) {
+                v = wait_level(pj, st, timeout_ns);
+                if (v < 0) bail = true;
             }
+            m = max(m, v);
         }
-        ok = grid_barrier(st, (++bar) * gridDim.x, timeout_ns, m);
-        const int32_t sz = ok ? (int32_t)ld_relaxed_u32(next_cnt) : 0;
-        lo = hi;
-        hi += sz;
-        ++m;
+        m = __reduce_max_sync(FULL_MASK, m);
+        if (__any_sync(FULL_MASK, bail)) break;
+        if (lane == 0) {
+            asm volatile("st.volatile.global.b32 [%0], %1;" ::"l"(level + i), "r"(m + 1)
+                         : "memory");
+        }
+        deepest = max(deepest, m + 1);
     }
-    if (gtid == 0) {
-        level_start[m] = lo;
-        *nlev_out = ok ? m : -1;
-    }
-    grid_exit(st);
+    if (lane == 0 && deepest >= 0) atomicMax(nlev_out, deepest + 1);
+}
+
+// level_ptr[l] = first position of level l in perm (rows ordered by level);
+// every level between 0 and the deepest holds a row, so each level starts
+// where the level of the previous position changes.
+__global__ void level_ptr_kernel(int32_t n, const int32_t *__restrict__ level,
+                                 const int32_t *__restrict__ perm, int32_t nlev,
+                                 int32_t *__restrict__ level_ptr) {
+    const int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > n) return;
+    const int32_t cur = p < n ? level[perm[p]] : nlev;
+    const int32_t prev = p > 0 ? level[perm[p - 1]] : -1;
+    for (int32_t l = prev + 1; l <= cur; ++l) level_ptr[l] = p;
 }
 
 // ---------------------------------------------------------------------------
@@ -242,40 +235,31 @@ cudaError_t launch_validate(int32_t n, int64_t nnz, const int32_t *row_ptr,
     return cudaGetLastError();
 }
 
-cudaError_t launch_count_succ(int32_t n, const int32_t *row_ptr, const int32_t *col,
-                              int32_t *tcnt, cudaStream_t s) {
+cudaError_t launch_levels_syncfree(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                                   int32_t *level, int32_t *nlev_out, DevStatus *st,
+                                   uint64_t timeout_ns, int num_sms, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    count_succ_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, row_ptr, col, tcnt);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fill_succ(int32_t n, const int32_t *row_ptr, const int32_t *col,
-                             const int32_t *tptr, int32_t *tcur, int32_t *tidx,
-                             cudaStream_t s) {
-    if (n == 0) return cudaSuccess;
-    fill_succ_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, row_ptr, col, tptr, tcur, tidx);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_bfs_levels(int32_t n, const int32_t *tptr, const int32_t *tidx,
-                              int32_t *indeg, int32_t *level, int32_t *queue,
-                              int32_t *cnt3, int32_t *level_start,
-                              int32_t *nlev_out, DevStatus *st,
-                              uint64_t timeout_ns, int num_sms, cudaStream_t s) {
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, bfs_levels_kernel, kBfsThreads, 0);
+        &per_sm, levels_syncfree_kernel, kLevThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-    // one CTA per SM keeps the barrier cheap; the frontier loop is grid-strided
-    int grid = num_sms;
-    int64_t want = ((int64_t)n + kBfsThreads - 1) / kBfsThreads;
-    if (want < grid) grid = (int)(want > 0 ? want : 1);
-    void *args[] = {(void *)&n, (void *)&tptr, (void *)&tidx, (void *)&indeg,
-                    (void *)&level, (void *)&queue, (void *)&cnt3, (void *)&level_start,
+    int64_t grid = (int64_t)per_sm * num_sms;
+    const int64_t want = ((int64_t)n * 32 + kLevThreads - 1) / kLevThreads;
+    if (want < grid) grid = want;
+    if ((e = cudaMemsetAsync(level, 0xff, (size_t)n * sizeof(int32_t), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(nlev_out, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+    void *args[] = {(void *)&n, (void *)&row_ptr, (void *)&col, (void *)&level,
                     (void *)&nlev_out, (void *)&st, (void *)&timeout_ns};
-    return cudaLaunchCooperativeKernel((void *)bfs_levels_kernel, dim3(grid),
-                                       dim3(kBfsThreads), args, 0, s);
+    return cudaLaunchCooperativeKernel((void *)levels_syncfree_kernel, dim3((unsigned)grid),
+                                       dim3(kLevThreads), args, 0, s);
+}
+
+cudaError_t launch_level_ptr(int32_t n, const int32_t *level, const int32_t *perm, int32_t nlev,
+                             int32_t *level_ptr, cudaStream_t s) {
+    level_ptr_kernel<<<(unsigned)(((int64_t)n + 256) / 256), 256, 0, s>>>(n, level, perm, nlev,
+                                                                        level_ptr);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_offdeg_hist(int32_t n, const int32_t *offdeg, unsigned long long *bins,

@@ -969,32 +969,12 @@ sptrsv_status_t sptrsv_analyze_ex(int32_t n, int64_t nnz, const int32_t *d_row_p
         CKP(cudaStreamSynchronize(s));
         for (int k = 0; k < 4; ++k) p->offdeg_hist[k] = (int64_t)hb[k];
     }
-    // successor lists (transpose of the strict lower part)
-    const int64_t nsucc = nnz - n;
-    DevArr<int32_t> tcnt, tptr, tcur, tidx;
-    DevArr<int64_t> stmp;
-    CKP(tcnt.alloc(n));
-    CKP(tptr.alloc((size_t)n + 1));
-    CKP(tcur.alloc(n));
-    CKP(tidx.alloc(nsucc > 0 ? nsucc : 1));
-    CKP(stmp.alloc(scan_tmp_elems(n)));
-    CKP(cudaMemsetAsync(tcnt.p, 0, n * sizeof(int32_t), s));
-    CKP(cudaMemsetAsync(tcur.p, 0, n * sizeof(int32_t), s));
-    CKP(launch_count_succ(n, p->row_ptr.p, p->col.p, tcnt.p, s));
-    CKP(exclusive_scan_i32_i32(tcnt.p, tptr.p, n, stmp.p, s));
-    CKP(launch_fill_succ(n, p->row_ptr.p, p->col.p, tptr.p, tcur.p, tidx.p, s));
-    // levels by breadth-first traversal
-    DevArr<int32_t> indeg, queue, cnt3, lstart, nlev_d;
-    CKP(indeg.alloc(n));
-    CKP(queue.alloc(n));
-    CKP(cnt3.alloc(3));
-    CKP(lstart.alloc((size_t)n + 1));
+    // levels of DAG_L by a synchronisation-free pass in row order
+    DevArr<int32_t> nlev_d;
     CKP(nlev_d.alloc(1));
     CKP(p->level.alloc(n));
-    CKP(cudaMemcpyAsync(indeg.p, p->offdeg.p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    CKP(cudaMemsetAsync(cnt3.p, 0, 3 * sizeof(int32_t), s));
-    CKP(launch_bfs_levels(n, tptr.p, tidx.p, indeg.p, p->level.p, queue.p, cnt3.p, lstart.p,
-                          nlev_d.p, p->status.p, timeout_ns(p), p->num_sms, s));
+    CKP(launch_levels_syncfree(n, p->row_ptr.p, p->col.p, p->level.p, nlev_d.p, p->status.p,
+                               timeout_ns(p), p->num_sms, s));
     int32_t nlev = 0;
     CKP(cudaMemcpyAsync(&nlev, nlev_d.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     {
@@ -1003,21 +983,20 @@ sptrsv_status_t sptrsv_analyze_ex(int32_t n, int64_t nnz, const int32_t *d_row_p
     }
     if (nlev <= 0) return fail(SPTRSV_ERR_BAD_STATE);
     p->nlev = nlev;
-    p->h_level_ptr.resize((size_t)nlev + 1);
-    CKP(cudaMemcpy(p->h_level_ptr.data(), lstart.p, ((size_t)nlev + 1) * sizeof(int32_t),
-                   cudaMemcpyDeviceToHost));
-    if (p->h_level_ptr[nlev] != n) return fail(SPTRSV_ERR_BAD_STATE);
-    CKP(p->level_ptr.alloc((size_t)nlev + 1));
-    CKP(cudaMemcpyAsync(p->level_ptr.p, lstart.p, ((size_t)nlev + 1) * sizeof(int32_t),
-                        cudaMemcpyDeviceToDevice, s));
-    // rows ordered by (level, row)
+    // rows ordered by (level, row), then the first position of every level
     CKP(p->perm.alloc(n));
+    CKP(p->level_ptr.alloc((size_t)nlev + 1));
     {
         DevArr<char> rtmp;
         CKP(rtmp.alloc(radix_tmp_bytes(n)));
         CKP(launch_level_perm(n, p->level.p, nlev, p->perm.p, rtmp.p, s));
+        CKP(launch_level_ptr(n, p->level.p, p->perm.p, nlev, p->level_ptr.p, s));
         CKP(cudaStreamSynchronize(s));
     }
+    p->h_level_ptr.resize((size_t)nlev + 1);
+    CKP(cudaMemcpy(p->h_level_ptr.data(), p->level_ptr.p, ((size_t)nlev + 1) * sizeof(int32_t),
+                   cudaMemcpyDeviceToHost));
+    if (p->h_level_ptr[nlev] != n) return fail(SPTRSV_ERR_BAD_STATE);
     // plain level-set structure
     {
         sptrsv_status_t st = choose_segments(p, s);

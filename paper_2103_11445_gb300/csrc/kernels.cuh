@@ -28,20 +28,15 @@ cudaError_t launch_validate(int32_t n, int64_t nnz, const int32_t *row_ptr,
                             const int32_t *col, const double *val,
                             int32_t *offdeg, unsigned long long *err,
                             unsigned long long *lnorm, cudaStream_t s);
-// Successor (transposed strict-lower) lists.
-cudaError_t launch_count_succ(int32_t n, const int32_t *row_ptr, const int32_t *col,
-                              int32_t *tcnt, cudaStream_t s);
-cudaError_t launch_fill_succ(int32_t n, const int32_t *row_ptr, const int32_t *col,
-                             const int32_t *tptr, int32_t *tcur, int32_t *tidx,
-                             cudaStream_t s);
-// Level analysis by breadth-first traversal (Kahn) in one cooperative
-// launch.  indeg is consumed.  level_start[0..nlev] receives the queue
-// offset of every level, *nlev_out the level count.  cnt3 = 3 zeroed ints.
-cudaError_t launch_bfs_levels(int32_t n, const int32_t *tptr, const int32_t *tidx,
-                              int32_t *indeg, int32_t *level, int32_t *queue,
-                              int32_t *cnt3, int32_t *level_start,
-                              int32_t *nlev_out, DevStatus *st,
-                              uint64_t timeout_ns, int num_sms, cudaStream_t s);
+// Level analysis by a synchronisation-free pass in row order (one
+// cooperative launch, no barrier per level): level[i] for every row,
+// *nlev_out = 1 + deepest level.  level and nlev_out are initialised here.
+cudaError_t launch_levels_syncfree(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                                   int32_t *level, int32_t *nlev_out, DevStatus *st,
+                                   uint64_t timeout_ns, int num_sms, cudaStream_t s);
+// level_ptr[0..nlev] from the level-ordered permutation.
+cudaError_t launch_level_ptr(int32_t n, const int32_t *level, const int32_t *perm, int32_t nlev,
+                             int32_t *level_ptr, cudaStream_t s);
 // histogram of rows by off-diagonal count (bins 0 | 1-2 | 3-6 | >= 7)
 cudaError_t launch_offdeg_hist(int32_t n, const int32_t *offdeg, unsigned long long *bins,
                                cudaStream_t s);
