@@ -1,4 +1,4 @@
-"""GPU parity of the level analysis (validation, BFS levels, level-ordered
+"""GPU parity of the level analysis (validation, levels, level-ordered
 permutation) against the oracle: integer outputs must match bit for bit."""
 import numpy as np
 import pytest
