@@ -185,3 +185,49 @@ def test_selection_hand_example():
     capped = lambda lv, r: None if lv == 3 else 10 * r
     assert rw.select_segments(rows, capped, 2, 2, 1.0, big) == [(0, 1), (2, 0), (3, 2)]
     assert rw.select_segments(rows, cost, 2, 0, 1.0, big) == [(i, 0) for i in range(6)]
+
+
+# --- the paper's worked example, as stated in the text (tests/golden) -----------
+
+def load_fig2_golden():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "fig2_rewriting.txt")
+    deps, levels, steps = {}, {}, []
+    with open(path) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if not line:
+                continue
+            key, rest = line.split(" ", 1)
+            if key == "dependency":
+                r, ds = rest.split(":")
+                deps[int(r)] = [int(v) for v in ds.split()]
+            elif key == "level":
+                r, lv = rest.split()
+                levels[int(r)] = int(lv)
+            elif key == "step":
+                sub, out = rest.split("->")
+                x, b, lv = (part.split() for part in out.split("|"))
+                steps.append(([int(v) for v in sub.split()], [int(v) for v in x],
+                              [int(v) for v in b], int(lv[0])))
+    return deps, levels, steps
+
+
+def test_fig2_golden_structure():
+    """The dependency moves the paper describes for row 3 (Sec. III): one
+    substitution (row 1) leaves a dependency on row 0 and lifts row 3 one
+    level; the second (row 0) leaves no dependency at all."""
+    deps, levels, steps = load_fig2_golden()
+    A, _ = fig2_matrix()   # rows 0, 1, 3 with exactly these dependencies (+ row 2)
+    for r, ds in deps.items():
+        a, e = A.row_ptr[r], A.row_ptr[r + 1] - 1
+        assert A.col[a:e].tolist() == ds
+    lv, _ = oracle.levels(A)
+    for r, l in levels.items():
+        assert lv[r] == l
+    for sub, x, b, new_level in steps:
+        t = new_level   # rewriting to target level t eliminates rows at levels >= t
+        row = rw.rewrite_row(A, lv, 3, t)
+        assert sorted(row.bcol.tolist()) == sorted(sub) == sorted(b)
+        assert row.xcol.tolist() == x
+        assert max([lv[j] + 1 for j in x], default=0) == new_level
