@@ -305,7 +305,8 @@ def make_from_spec(spec: dict) -> CSR:
         return banded(spec["n"], seed=spec["seed"],
                       per_row=spec.get("per_row", 8))
     if fam == "thin_tail":
-        return thin_tail(spec["n"], seed=spec["seed"])
+        return thin_tail(spec["n"], seed=spec["seed"], per_row=spec.get("per_row", 8),
+                         chain_frac=spec.get("chain_frac", 0.05))
     raise ValueError(f"unknown family {fam}")
 
 
@@ -314,6 +315,30 @@ def costmodel_specs(count: int = 2000, seed: int = 5000) -> list[dict]:
     ``batch_specs``, random-banded rows with 5..20 off-diagonal entries."""
     return batch_specs(count, seed=seed, n_lo=1e4, n_hi=5e5, nrhs_max=1,
                        band_range=(5, 20))
+
+
+def costmodel_large_specs(count: int = 80, seed: int = 7000) -> list[dict]:
+    """Larger matrices for the cost model's training set only: n log-uniform
+    in [5e5, 2.5e6], family uniform in {5-point, 7-point, random-banded,
+    thin-tail} (thin tails with a chain of 1-10 % of the rows)."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for m in range(count):
+        n = float(np.exp(rng.uniform(np.log(5e5), np.log(2.5e6))))
+        fam = ("stencil2d", "stencil3d", "banded", "thin_tail")[int(rng.integers(0, 4))]
+        per_row = int(rng.integers(5, 13))
+        if fam == "stencil2d":
+            side = int(round(n ** 0.5))
+            n_adj = side * side
+        elif fam == "stencil3d":
+            side = int(round(n ** (1.0 / 3.0)))
+            n_adj = side ** 3
+        else:
+            side = 0
+            n_adj = int(round(n))
+        specs.append(dict(index=m, family=fam, n=n_adj, side=side, nrhs=1, per_row=per_row,
+                          chain_frac=float(rng.uniform(0.01, 0.10)), seed=seed + m))
+    return specs
 
 
 def config_matrix(index: int, small: bool = False) -> CSR:

@@ -10,9 +10,10 @@ Heuristic H remains the fallback when no network is attached, and the
 baseline the network is judged against.
 
 Training data come from the solver itself: for every seeded synthetic matrix
-(``matgen`` mixtures) and every depth, the library's features of that
+(``matgen`` mixtures) and every candidate, the library's features of that
 candidate and the measured time of the library's own solve of the rewritten
-plan (median of a few solves, L2 flushed before each).
+plan (the faster of two launch shapes, median of a few solves each, L2
+flushed before each).
 
     python -m paper_2103_11445_gb300.costmodel collect --count 600 --out data.npz
     python -m paper_2103_11445_gb300.costmodel train --data data.npz --out weights.npz
@@ -36,8 +37,12 @@ THIN_BUDGET = 4.0
 N_FEATURES = 17
 HIDDEN = 64
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "costmodel_weights.npz")
-# launch shape used for the timing labels and for the model's own plans
-LABEL_LAUNCH = dict(solve_mode=B.SOLVE_SYNCFREE, block_threads=128, lanes_per_row=0)
+# Launch shapes of the timing labels: a label is the fastest of these
+# (sync-free kernel, 128 threads per CTA): one lane per row on one CTA per
+# SM, and four lanes per row on four CTAs per SM -- between them the shapes
+# the autotuner ends up with on the matrices measured (deep chains vs wide
+# levels), at a fraction of a full autotuning run per candidate.
+LABEL_LAUNCHES = (dict(lanes_per_row=1, ctas_per_sm=1), dict(lanes_per_row=4, ctas_per_sm=4))
 
 
 def init_params(n_in: int = N_FEATURES, hidden: int = HIDDEN, seed: int = 0) -> np.ndarray:
@@ -143,9 +148,19 @@ def time_solves(plan: "B.Plan", n: int, reps: int = 5) -> float:
     return statistics.median(ts)
 
 
-def heuristic_time(plan: "B.Plan", n: int, reps: int = 5) -> float:
-    plan.transform(select_mode=B.SELECT_HEURISTIC, **LABEL_LAUNCH)
-    return time_solves(plan, n, reps)
+def label_time(plan: "B.Plan", n: int, reps: int = 3, **select) -> float:
+    """The label of a selection: its fastest solve over LABEL_LAUNCHES (us)."""
+    sms = plan.info()["num_sms"]
+    best = float("inf")
+    for lk in LABEL_LAUNCHES:
+        plan.transform(**select, solve_mode=B.SOLVE_SYNCFREE, block_threads=128,
+                       lanes_per_row=lk["lanes_per_row"], grid_blocks=lk["ctas_per_sm"] * sms)
+        best = min(best, time_solves(plan, n, reps))
+    return best
+
+
+def heuristic_time(plan: "B.Plan", n: int, reps: int = 3) -> float:
+    return label_time(plan, n, reps, select_mode=B.SELECT_HEURISTIC)
 
 
 def candidate_kw(code: int) -> dict:
@@ -158,7 +173,7 @@ def candidate_kw(code: int) -> dict:
     return dict(select_mode=B.SELECT_FIXED, depth=code)
 
 
-def collect(specs, reps: int = 5, with_heuristic: bool = True, log=None):
+def collect(specs, reps: int = 3, with_heuristic: bool = True, log=None):
     """Features and measured log2 times (us) for every spec and candidate."""
     import matgen as mg
     X, y, group, hs = [], [], [], []
@@ -167,8 +182,7 @@ def collect(specs, reps: int = 5, with_heuristic: bool = True, log=None):
         P = B.Plan(A.n, A.row_ptr, A.col, A.val)
         feats = B.sptrsv_costmodel_features(P.handle, CANDIDATES)
         for code, f in zip(CANDIDATES, feats):
-            P.transform(**candidate_kw(code), **LABEL_LAUNCH)
-            us = time_solves(P, A.n, reps)
+            us = label_time(P, A.n, reps, **candidate_kw(code))
             X.append(f)
             y.append(np.log2(us))
             group.append(k)
@@ -206,7 +220,9 @@ def main(argv=None) -> int:
     c.add_argument("--count", type=int, default=600)
     c.add_argument("--seed", type=int, default=5000)
     c.add_argument("--n-hi", type=float, default=5e5)
-    c.add_argument("--reps", type=int, default=5)
+    c.add_argument("--reps", type=int, default=3)
+    c.add_argument("--large", type=int, default=0,
+                   help="collect this many larger matrices (training-only set) instead")
     c.add_argument("--out", required=True)
     t = sub.add_parser("train")
     t.add_argument("--data", required=True)
@@ -214,14 +230,19 @@ def main(argv=None) -> int:
     t.add_argument("--train-frac", type=float, default=0.8)
     t.add_argument("--epochs", type=int, default=4000)
     t.add_argument("--lr", type=float, default=3e-3)
+    t.add_argument("--extra", default=None,
+                   help="additional training-only data (e.g. the larger matrices)")
     args = ap.parse_args(argv)
     import torch
     torch.cuda.set_device(0)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import matgen as mg
     if args.cmd == "collect":
-        specs = mg.batch_specs(args.count, seed=args.seed, n_lo=1e4, n_hi=args.n_hi,
-                               nrhs_max=1, band_range=(5, 20))
+        if args.large:
+            specs = mg.costmodel_large_specs(args.large)
+        else:
+            specs = mg.batch_specs(args.count, seed=args.seed, n_lo=1e4, n_hi=args.n_hi,
+                                   nrhs_max=1, band_range=(5, 20))
         t0 = time.time()
         X, y, g, h = collect(specs, reps=args.reps, log=lambda s: print(s, flush=True))
         np.savez(args.out, X=X, y=y, group=g, h=h, candidates=np.array(CANDIDATES),
@@ -233,8 +254,13 @@ def main(argv=None) -> int:
     ng = int(g.max()) + 1
     cut = int(round(ng * args.train_frac))
     tr, te = g < cut, g >= cut
+    Xt, yt = X[tr], y[tr]
+    if args.extra:
+        e = np.load(args.extra)
+        Xt, yt = np.concatenate([Xt, e["X"]]), np.concatenate([yt, e["y"]])
+        print(f"training set: {int(tr.sum())} + {len(e['y'])} extra rows")
     m = CostModel()
-    hist = m.fit(X[tr], y[tr], epochs=args.epochs, lr=args.lr, log_every=500)
+    hist = m.fit(Xt, yt, epochs=args.epochs, lr=args.lr, log_every=500)
     for e, l in hist:
         print(f"epoch {e}: train mse {l:.4f}")
     te_mse = float(np.mean((m.predict(X[te]) - y[te]) ** 2))

@@ -29,16 +29,15 @@ def test_trained_network_beats_the_heuristic():
         A = mg.make_from_spec(sp)
         P = B.Plan(A.n, A.row_ptr, A.col, A.val)
         net.attach(P)
-        P.transform(select_mode=B.SELECT_COSTMODEL, **cm.LABEL_LAUNCH)
+        P.transform(select_mode=B.SELECT_COSTMODEL, solve_mode=B.SOLVE_SYNCFREE)
         picks.append(P.info()["chosen_depth"])
         b = mg.rhs_uniform(A.n, seed=sp["seed"])
         x = P.solve(torch.as_tensor(b, device="cuda"))
         P.check()
         assert oracle.relerr(x.cpu().numpy(), oracle.forward_subst(A, b)) <= 1e-10
-        t_cm.append(cm.time_solves(P, A.n, reps=7))
+        t_cm.append(cm.label_time(P, A.n, reps=7, select_mode=B.SELECT_COSTMODEL))
         t_h.append(cm.heuristic_time(P, A.n, reps=7))
-        P.transform(select_mode=B.SELECT_NONE, **cm.LABEL_LAUNCH)
-        t_plain.append(cm.time_solves(P, A.n, reps=7))
+        t_plain.append(cm.label_time(P, A.n, reps=7, select_mode=B.SELECT_NONE))
         P.close()
     net.close()
     geo = lambda a, b: float(np.exp(np.mean(np.log(np.asarray(a) / np.asarray(b)))))
