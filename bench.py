@@ -49,9 +49,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--side", type=int, default=128, help="grid side of the 3D stencil")
-    ap.add_argument("--workload", choices=["stencil3d", "thin_tail"], default="stencil3d",
+    ap.add_argument("--workload", choices=["stencil3d", "thin_tail", "batch256"],
+                    default="stencil3d",
                     help="stencil3d: the 3D 7-point lower triangle (default); thin_tail: the "
-                         "1M-row random-banded matrix with a near-serial 50k-row tail")
+                         "1M-row random-banded matrix with a near-serial 50k-row tail; "
+                         "batch256: 256 uneven matrices with 1-32 right-hand sides each, FP32 "
+                         "values + FP64 refinement, one graph-replayed launch")
     ap.add_argument("--depths", default="1,2,3,4,6",
                     help="fixed rewrite depths tried besides heuristic H")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -229,9 +232,11 @@ def oracle_solve_timed(A, b, seconds: float, min_runs: int = 3, max_runs: int = 
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
-    A, b = workload(args.side, args.workload)
     import oracle
     oracle.build()
+    if args.workload == "batch256":
+        return run_reference_batch(args)
+    A, b = workload(args.side, args.workload)
     for _ in range(max(args.warmup, 0)):
         oracle.forward_subst(A, b)
     times = []
@@ -253,6 +258,44 @@ def run_reference(args, world, rank):
                          "sample": f"{args.steps} full serial FP64 forward substitutions "
                                    f"(median), C oracle, 1 thread of "
                                    f"{len(os.sched_getaffinity(0))} available"},
+        "e2e": {"value": round(val, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_batch(args, sample: int = 16):
+    """The oracle on the batch workload: each step solves a bounded sample
+    (the first `sample` matrices, all their right-hand sides)."""
+    import oracle
+    import matgen as mg
+    specs, mats = batch_matrices()
+    mats, specs = mats[:sample], specs[:sample]
+    bs = [mg.rhs_uniform(A.n, nrhs=sp["nrhs"], seed=900 + sp["index"]).reshape(A.n, sp["nrhs"])
+          for A, sp in zip(mats, specs)]
+    B = sum(b_alg(A.n, A.nnz, b.shape[1]) for A, b in zip(mats, bs))
+    for _ in range(max(args.warmup, 0)):
+        for A, b in zip(mats, bs):
+            oracle.forward_subst(A, b)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for A, b in zip(mats, bs):
+            oracle.forward_subst(A, b)
+        times.append(time.perf_counter() - t0)
+    ms = statistics.median(times) * 1e3
+    val = B / (ms * 1e-3) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "batch256 (first 16 of the 256 matrices per step)",
+                   "b_alg_bytes": B},
+        "cpu_baseline": {"value": round(val, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"serial FP64 forward substitution of the first {sample} "
+                                   f"matrices of the batch, all right-hand sides, C oracle"},
         "e2e": {"value": round(val, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -523,6 +566,149 @@ def run_ours(args, world, rank, local):
     return 0
 
 
+def batch_matrices():
+    import matgen as mg
+    specs = mg.batch_specs(256, seed=4000)
+    return specs, [mg.make_from_spec(sp) for sp in specs]
+
+
+def run_batch(args, world, rank):
+    """256 uneven matrices in one persistent, graph-replayed launch (FP32
+    values, FP64 refinement to the 1e-10 bound); value = the summed
+    algorithmic bytes of all matrices and right-hand sides / time."""
+    import numpy as np
+    import torch
+    import matgen as mg
+    from paper_2103_11445_gb300 import binding as Bd
+    dev = torch.device("cuda", torch.cuda.current_device())
+    specs, mats = batch_matrices()
+    t0 = time.perf_counter()
+    plans = []
+    for A in mats:
+        P = Bd.Plan(A.n, A.row_ptr, A.col, A.val)
+        P.transform(select_mode=Bd.SELECT_HEURISTIC, solve_mode=Bd.SOLVE_SYNCFREE,
+                    precision=Bd.F32_IR)
+        plans.append(P)
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    h = Bd.sptrsv_batch_create([P.handle for P in plans])
+    nrhs = [sp["nrhs"] for sp in specs]
+    bnp = [mg.rhs_uniform(A.n, nrhs=k, seed=900 + sp["index"]).reshape(A.n, k)
+           for A, sp, k in zip(mats, specs, nrhs)]
+    bs = [torch.as_tensor(b, device=dev) for b in bnp]
+    xs = [torch.empty_like(b) for b in bs]
+    B = sum(b_alg(A.n, A.nnz, k) for A, k in zip(mats, nrhs))
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        Bd.sptrsv_batch_solve(h, [b.data_ptr() for b in bs], [x.data_ptr() for x in xs], nrhs,
+                              stream.cuda_stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+        uuid = None
+        try:
+            uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        except Exception:
+            pass
+        clocks = ClockSampler(uuid)
+        clocks.start()
+        barrier(world)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            step()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        clk = clocks.stop()
+    assert Bd.sptrsv_batch_check(h, stream.cuda_stream) == 0
+    info = Bd.sptrsv_batch_get_info(h, len(specs))
+    steps_ms = [a.elapsed_time(c) for a, c in ev]
+    ms = max_over_ranks(world, statistics.mean(steps_ms))
+    value = B * world / (ms * 1e-3) / 1e9
+    # parity: two columns of every matrix against the oracle
+    import oracle
+    worst = 0.0
+    for A, x, b, k in zip(mats, xs, bnp, nrhs):
+        cols = sorted({0, k - 1})
+        ref = oracle.forward_subst(A, np.ascontiguousarray(b[:, cols]))
+        worst = max(worst, oracle.relerr(x.cpu().numpy()[:, cols], ref))
+    # end to end: pinned host right-hand sides in, solutions out, every step
+    hb = [torch.from_numpy(b.copy()).pin_memory() for b in bnp]
+    hx = [torch.empty_like(b).pin_memory() for b in hb]
+    e2e_ms = []
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup + args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for d, src in zip(bs, hb):
+                d.copy_(src, non_blocking=True)
+            step()
+            for dst, src in zip(hx, xs):
+                dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= args.warmup:
+                e2e_ms.append(e0.elapsed_time(e1))
+    e2e = B * world / (max_over_ranks(world, statistics.mean(e2e_ms)) * 1e-3) / 1e9
+    io_bytes = int(sum(b.size * 8 for b in bnp))
+    # CPU oracle on a bounded sample of the matrices
+    import os as _os
+    t_cpu, b_cpu, i = 0.0, 0, 0
+    while t_cpu < args.cpu_seconds and i < len(mats):
+        A, b = mats[i], bnp[i]
+        t1 = time.perf_counter()
+        oracle.forward_subst(A, b)
+        t_cpu += time.perf_counter() - t1
+        b_cpu += b_alg(A.n, A.nnz, b.shape[1])
+        i += 1
+    peak, peak_kind = peaks()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "batch256 (256 matrices, n log-uniform in [1e3, 2e5], 5-point "
+                                   "/ 7-point / random-banded, 1-32 RHS each, FP32 values + FP64 "
+                                   "refinement to relerr 1e-10, one graph-replayed launch)",
+                       "b_alg_bytes": B, "rows": int(sum(A.n for A in mats)),
+                       "rhs_columns": int(sum(nrhs)), "selection": "heuristic",
+                       "converged": int(sum(info["converged"])),
+                       "refinement_steps_max": int(max(info["iters"])),
+                       "graph": info["graph"], "setup_ms": round(setup_ms, 1),
+                       "l2": "flushed before every step (256 MiB write, outside the events)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": round(value / world, 2), "peak": peak,
+                         "unit": "GB/s", "frac": round(value / world / peak, 4),
+                         "peak_kind": f"{peak_kind} copy bandwidth",
+                         "kernel": "batch_kernel<true> (one launch per step, CUDA events on "
+                                   "the launch stream)", "traffic": None},
+            "e2e": {"value": round(e2e, 3), "unit": "GB/s", "h2d_bytes_per_step": io_bytes,
+                    "d2h_bytes_per_step": io_bytes},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "cpu_baseline": {"value": round(b_cpu / t_cpu / 1e9, 4), "unit": "GB/s", "cores": 1,
+                             "kind": "oracle",
+                             "sample": f"serial FP64 forward substitution of the first {i} "
+                                       f"matrices (all their right-hand sides), C oracle, 1 of "
+                                       f"{len(_os.sched_getaffinity(0))} host cores"},
+            "relerr_vs_oracle": worst,
+        }
+        print(json.dumps(line), flush=True)
+    Bd.sptrsv_batch_destroy(h)
+    for P in plans:
+        P.close()
+    return 0
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -530,6 +716,8 @@ def main():
         rc = run_reference(args, world, rank)
     elif args.profile_run:
         rc = run_profile(args)
+    elif args.workload == "batch256":
+        rc = run_batch(args, world, rank)
     else:
         rc = run_ours(args, world, rank, local)
     if world > 1:

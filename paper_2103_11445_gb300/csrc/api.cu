@@ -610,9 +610,23 @@ sptrsv_status_t autotune(sptrsv_plan_t p, cudaStream_t s) {
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     int warm = 2, reps = 5;
+    double best_ms = 1e30;
     auto time_cfg = [&](double *ms_out) -> sptrsv_status_t {
         CKS(apply_config(p, s));
-        for (int w = 0; w < warm; ++w) CKS(solve_impl(p, b.p, x.p, 1, s));
+        // the first warm-up is timed: a shape four times slower than the best
+        // so far is dropped without further solves
+        CK(cudaEventRecord(e0, s));
+        CKS(solve_impl(p, b.p, x.p, 1, s));
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float first = 0;
+        CK(cudaEventElapsedTime(&first, e0, e1));
+        if (first > 4.0 * best_ms) {
+            CKS(sync_status(p, s));
+            *ms_out = first;
+            return SPTRSV_OK;
+        }
+        for (int w = 1; w < warm; ++w) CKS(solve_impl(p, b.p, x.p, 1, s));
         std::vector<float> t;
         for (int r = 0; r < reps; ++r) {
             CK(cudaEventRecord(e0, s));
@@ -639,7 +653,6 @@ sptrsv_status_t autotune(sptrsv_plan_t p, cudaStream_t s) {
                a.backoff_ns == c.backoff_ns;
     };
     SolveConfig best = p->cfg;
-    double best_ms = 1e30;
     auto trial = [&](const SolveConfig &c, double *ms) -> sptrsv_status_t {
         for (const Trial &t : tried)
             if (same(t.c, c)) {
@@ -651,13 +664,13 @@ sptrsv_status_t autotune(sptrsv_plan_t p, cudaStream_t s) {
         if (c.grid > 0 && grid_for(p, 1, f32) < c.grid) return SPTRSV_OK;  // not co-resident
         CKS(time_cfg(ms));
         tried.push_back({c, *ms});
-        if (*ms > 5.0) {  // long solves: fewer repetitions
-            warm = 1;
-            reps = 3;
-        }
         if (*ms < best_ms) {
             best_ms = *ms;
             best = c;
+        }
+        if (best_ms > 5.0) {  // long solves: fewer repetitions
+            warm = 1;
+            reps = 3;
         }
         return SPTRSV_OK;
     };

@@ -293,25 +293,57 @@ __device__ __forceinline__ bool chunk_multi(const SolveData<T> &sd, int32_t c, T
             brow = (T)load_rhs(cx, (int64_t)row * cx.ld + r);
             acc = brow;
         }
-        if (rowok) {
+        if (active) {
+            // the row's entries in storage order, U at a time: U loads of
+            // entries, then U loads of x (or b) values in flight together,
+            // then the waits and FMAs (terms already computed first)
             const int64_t base = mt.w + (int64_t)k * L;
-            for (int step = 0; step < mt.z; ++step) {
-                for (int sub = 0; sub < L; ++sub) {
-                    const int64_t slot = base + (int64_t)step * stride + sub;
-                    const int32_t cc = __ldg(sd.ecol + slot);
-                    if (cc == PAD_COL || !active) continue;
-                    const T v = __ldg(sd.eval + slot);
-                    T xv;
-                    if (cc >= 0) {
-                        T *px = out + (int64_t)cc * cx.ld + r;
-                        xv = load_x<T, SF>(px);
-                        if (SF && Bits<T>::of(xv) == Sentinel<T>::bits)
-                            xv = wait_x<T>(px, cx.st, cx.timeout_ns, cx.backoff_ns, bail);
-                    } else {
-                        xv = other_term<T>(cx, cc, out, r);
-                    }
-                    acc = fma(-v, xv, acc);
+            const int nent = mt.z * L;
+            auto slot_of = [&](int j) { return base + (int64_t)(j / L) * stride + (j % L); };
+            constexpr int U = 4;
+            int j = 0;
+            for (; j + U <= nent; j += U) {
+                int32_t cc[U];
+                T vv[U], xv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t sl = slot_of(j + u);
+                    cc[u] = __ldg(sd.ecol + sl);
+                    vv[u] = __ldg(sd.eval + sl);
                 }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (cc[u] >= 0) xv[u] = load_x<T, SF>(out + (int64_t)cc[u] * cx.ld + r);
+                    else xv[u] = other_term<T>(cx, cc[u], out, r);
+                }
+                bool pend[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    pend[u] = SF && cc[u] >= 0 && Bits<T>::of(xv[u]) == Sentinel<T>::bits;
+                    if (!pend[u]) acc = fma(-vv[u], xv[u], acc);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (pend[u])
+                        acc = fma(-vv[u],
+                                  wait_x<T>(out + (int64_t)cc[u] * cx.ld + r, cx.st,
+                                            cx.timeout_ns, cx.backoff_ns, bail),
+                                  acc);
+            }
+            for (; j < nent; ++j) {
+                const int64_t sl = slot_of(j);
+                const int32_t cc = __ldg(sd.ecol + sl);
+                const T v = __ldg(sd.eval + sl);
+                T xv;
+                if (cc >= 0) {
+                    T *px = out + (int64_t)cc * cx.ld + r;
+                    xv = load_x<T, SF>(px);
+                    if (SF && Bits<T>::of(xv) == Sentinel<T>::bits)
+                        xv = wait_x<T>(px, cx.st, cx.timeout_ns, cx.backoff_ns, bail);
+                } else {
+                    xv = other_term<T>(cx, cc, out, r);
+                }
+                acc = fma(-v, xv, acc);
             }
         }
         if (active)
