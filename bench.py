@@ -584,10 +584,10 @@ def run_batch(args, world, rank):
     specs, mats = batch_matrices()
     t0 = time.perf_counter()
     plans = []
-    for A in mats:
+    for A, sp in zip(mats, specs):
         P = Bd.Plan(A.n, A.row_ptr, A.col, A.val)
         P.transform(select_mode=Bd.SELECT_HEURISTIC, solve_mode=Bd.SOLVE_SYNCFREE,
-                    precision=Bd.F32_IR)
+                    precision=Bd.F32_IR, nrhs_hint=sp["nrhs"])
         plans.append(P)
     setup_ms = (time.perf_counter() - t0) * 1e3
     h = Bd.sptrsv_batch_create([P.handle for P in plans])

@@ -116,6 +116,12 @@ typedef struct {
     int32_t poll_backoff_ns; /* synchronisation-free solve: sleep between
                                 polls of an unready unknown; 0 = none,
                                 < 0 = auto */
+    int32_t nrhs_hint;       /* right-hand sides a solve usually carries
+                                (1..32; default 1).  Above 1 the structure is
+                                laid out for that many columns (one warp lane
+                                per column and row, a chunk's rows in one
+                                pass) and the autotuner times solves with
+                                that many columns; any nrhs still works. */
 } sptrsv_transform_params_t;
 
 /* Everything a caller may want to report about a plan. */

@@ -45,7 +45,7 @@ class TransformParams(Structure):
         ("precision", c_int32), ("ir_tol", c_double), ("ir_max_iter", c_int32),
         ("lanes_per_row", c_int32), ("block_threads", c_int32),
         ("cta_run_rows", c_int32), ("wait_timeout_ms", c_int32),
-        ("grid_blocks", c_int32), ("poll_backoff_ns", c_int32),
+        ("grid_blocks", c_int32), ("poll_backoff_ns", c_int32), ("nrhs_hint", c_int32),
     ]
 
 

@@ -601,11 +601,13 @@ sptrsv_status_t autotune(sptrsv_plan_t p, cudaStream_t s) {
     const int32_t n = p->n;
     if (n == 0) return SPTRSV_OK;
     const bool f32 = p->prm.precision == SPTRSV_F32_IR;
+    const int nrt = p->prm.nrhs_hint;  // columns of the trial solves
     DevArr<double> b, x;
-    CK(b.alloc(n));
-    CK(x.alloc(n));
-    std::vector<double> ones(n, 1.0);
-    CK(cudaMemcpyAsync(b.p, ones.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(b.alloc((size_t)n * nrt));
+    CK(x.alloc((size_t)n * nrt));
+    std::vector<double> ones((size_t)n * nrt, 1.0);
+    CK(cudaMemcpyAsync(b.p, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice,
+                       s));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -616,7 +618,7 @@ sptrsv_status_t autotune(sptrsv_plan_t p, cudaStream_t s) {
         // the first warm-up is timed: a shape four times slower than the best
         // so far is dropped without further solves
         CK(cudaEventRecord(e0, s));
-        CKS(solve_impl(p, b.p, x.p, 1, s));
+        CKS(solve_impl(p, b.p, x.p, nrt, s));
         CK(cudaEventRecord(e1, s));
         CK(cudaEventSynchronize(e1));
         float first = 0;
@@ -626,11 +628,11 @@ sptrsv_status_t autotune(sptrsv_plan_t p, cudaStream_t s) {
             *ms_out = first;
             return SPTRSV_OK;
         }
-        for (int w = 1; w < warm; ++w) CKS(solve_impl(p, b.p, x.p, 1, s));
+        for (int w = 1; w < warm; ++w) CKS(solve_impl(p, b.p, x.p, nrt, s));
         std::vector<float> t;
         for (int r = 0; r < reps; ++r) {
             CK(cudaEventRecord(e0, s));
-            CKS(solve_impl(p, b.p, x.p, 1, s));
+            CKS(solve_impl(p, b.p, x.p, nrt, s));
             CK(cudaEventRecord(e1, s));
             CK(cudaEventSynchronize(e1));
             float ms = 0;
@@ -661,7 +663,7 @@ sptrsv_status_t autotune(sptrsv_plan_t p, cudaStream_t s) {
             }
         *ms = 1e30;
         p->cfg = c;
-        if (c.grid > 0 && grid_for(p, 1, f32) < c.grid) return SPTRSV_OK;  // not co-resident
+        if (c.grid > 0 && grid_for(p, nrt, f32) < c.grid) return SPTRSV_OK;  // not co-resident
         CKS(time_cfg(ms));
         tried.push_back({c, *ms});
         if (*ms < best_ms) {
@@ -686,6 +688,7 @@ sptrsv_status_t autotune(sptrsv_plan_t p, cudaStream_t s) {
     std::vector<int> lanes = {1, 2, 4};
     const int la = auto_lanes(p);
     if (la > 4) lanes.push_back(la);
+    if (nrt > 1) lanes = {p->cfg.L};  // laid out for the hinted columns
     // stage 1: lanes x mode at three launch shapes
     struct Pair {
         SolveConfig c;
@@ -752,6 +755,8 @@ void resolve_params(sptrsv_plan_t p, const sptrsv_transform_params_t *in) {
     if (q.ir_max_iter < 0) q.ir_max_iter = 8;
     if (q.ir_max_iter > 64) q.ir_max_iter = 64;
     if (q.wait_timeout_ms <= 0) q.wait_timeout_ms = 5000;
+    if (q.nrhs_hint < 1) q.nrhs_hint = 1;
+    if (q.nrhs_hint > 32) q.nrhs_hint = 32;
     p->prm = q;
     p->thin_rows_used = q.thin_rows;
 }
@@ -852,6 +857,7 @@ void sptrsv_default_params(sptrsv_transform_params_t *prm) {
     prm->wait_timeout_ms = 5000;
     prm->grid_blocks = 0;
     prm->poll_backoff_ns = -1;
+    prm->nrhs_hint = 1;
 }
 
 sptrsv_status_t sptrsv_analyze(int32_t n, int64_t nnz, const int32_t *d_row_ptr,
@@ -1066,6 +1072,11 @@ sptrsv_status_t sptrsv_transform(sptrsv_plan_t p, const sptrsv_transform_params_
     CKS(build_struct<double>(p, p->s64, 1, s));
     CKS(count_terms(p, s));
     c.L = p->prm.lanes_per_row > 0 ? p->prm.lanes_per_row : auto_lanes(p);
+    if (p->prm.nrhs_hint > 1 && p->prm.lanes_per_row <= 0) {
+        // several columns: one lane per (row, column), a chunk's rows in one pass
+        c.L = 1;
+        while (c.L < p->prm.nrhs_hint) c.L *= 2;
+    }
     c.cta_run_rows = p->prm.cta_run_rows < 0 ? 0
                      : p->prm.cta_run_rows > 0 ? p->prm.cta_run_rows
                                                : c.block_threads / c.L;

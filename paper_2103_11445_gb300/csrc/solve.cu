@@ -311,6 +311,7 @@ __device__ __forceinline__ bool chunk_multi(const SolveData<T> &sd, int32_t c, T
                     cc[u] = __ldg(sd.ecol + sl);
                     vv[u] = __ldg(sd.eval + sl);
                 }
+                if (cc[0] == PAD_COL) break;  // a row's entries come first, pads after
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     if (cc[u] >= 0) xv[u] = load_x<T, SF>(out + (int64_t)cc[u] * cx.ld + r);
@@ -333,6 +334,7 @@ __device__ __forceinline__ bool chunk_multi(const SolveData<T> &sd, int32_t c, T
             for (; j < nent; ++j) {
                 const int64_t sl = slot_of(j);
                 const int32_t cc = __ldg(sd.ecol + sl);
+                if (cc == PAD_COL) break;
                 const T v = __ldg(sd.eval + sl);
                 T xv;
                 if (cc >= 0) {

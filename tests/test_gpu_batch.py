@@ -11,13 +11,15 @@ pytestmark = pytest.mark.gpu
 TOL64 = 1e-10
 
 
-def build(specs, precision, **kw):
+def build(specs, precision, hint=False, **kw):
     import torch
     from paper_2103_11445_gb300 import binding as B
     plans, mats = [], []
     for sp in specs:
         A = mg.make_from_spec(sp)
         P = B.Plan(A.n, A.row_ptr, A.col, A.val)
+        if hint:
+            kw = dict(kw, nrhs_hint=sp["nrhs"])
         P.transform(precision=precision, **kw)
         plans.append(P)
         mats.append(A)
@@ -98,7 +100,7 @@ def test_batch_256_uneven_matrices():
     import torch
     from paper_2103_11445_gb300 import binding as B
     specs = mg.batch_specs(256, seed=4000)
-    plans, mats = build(specs, 1, select_mode=1, solve_mode=2)
+    plans, mats = build(specs, 1, hint=True, select_mode=1, solve_mode=2)
     h = B.sptrsv_batch_create([P.handle for P in plans])
     stream = torch.cuda.Stream()
     bs, xs, bnp = run_batch(plans, mats, specs, 9, stream)

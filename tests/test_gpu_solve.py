@@ -46,6 +46,21 @@ def test_multi_rhs(mode, nrhs):
 
 
 @pytest.mark.parametrize("mode", B_MODES, ids=B_IDS)
+@pytest.mark.parametrize("hint,nrhs", [(4, 3), (8, 8), (32, 32), (32, 5), (2, 40)])
+def test_multi_rhs_layout_hint(mode, hint, nrhs):
+    """A structure laid out for `hint` columns (nrhs_hint), rewritten, solved
+    with nrhs columns (the hint is only a layout choice)."""
+    A = mg.thin_tail(6000, seed=77)
+    P = plan_for(A, select_mode=3, depth=2, nrhs_hint=hint, **mode)
+    L = 1
+    while L < hint:
+        L *= 2
+    assert P.info()["lanes_per_row"] == L
+    b = mg.rhs_uniform(A.n, nrhs=nrhs, seed=hint)
+    assert_close_to_oracle(A, gpu_solve(P, b), b, TOL64)
+
+
+@pytest.mark.parametrize("mode", B_MODES, ids=B_IDS)
 def test_closed_forms(mode):
     n = 3000
     ident = mg.CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.ones(n))
