@@ -147,6 +147,9 @@ typedef struct {
                                 (-1 when it did not run) */
     double analyze_ms, transform_ms;
     int32_t op;              /* SPTRSV_OP_* of the plan */
+    int32_t tuned_from_cache; /* 1: the last SOLVE_AUTO transform reused the launch
+                                 tuned earlier in this process for a plan of the
+                                 same shape (sptrsv_autotune_cache_clear) */
 } sptrsv_info_t;
 
 SPTRSV_API const char *sptrsv_status_string(sptrsv_status_t s);
@@ -208,6 +211,12 @@ SPTRSV_API sptrsv_status_t sptrsv_transform(sptrsv_plan_t p, const sptrsv_transf
  * of the values and refines with FP64 residuals of the original L. */
 SPTRSV_API sptrsv_status_t sptrsv_solve(sptrsv_plan_t p, const double *d_b, double *d_x,
                              int32_t nrhs, sptrsv_stream_t stream);
+
+/* SPTRSV_SOLVE_AUTO keeps each tuned launch configuration in a process-wide
+ * cache keyed by the device, the plan's shape (rows, entries, level sizes,
+ * chosen segments, terms of the structure) and the requested constraints, so
+ * a later transform of the same shape skips the timing.  This empties it. */
+SPTRSV_API void sptrsv_autotune_cache_clear(void);
 
 /* Synchronise `stream` and return the error latched by a kernel, if any. */
 SPTRSV_API sptrsv_status_t sptrsv_check(sptrsv_plan_t p, sptrsv_stream_t stream);

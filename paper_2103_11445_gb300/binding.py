@@ -61,6 +61,7 @@ class Info(Structure):
         ("ir_iters_last", c_int32), ("num_sms", c_int32), ("poll_backoff_ns", c_int32),
         ("chosen_depth", c_int32),
         ("analyze_ms", c_double), ("transform_ms", c_double), ("op", c_int32),
+        ("tuned_from_cache", c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -78,6 +79,7 @@ _SIGS = {
                                  c_void_p, POINTER(c_void_p)]),
     "sptrsv_analyze_ex": (c_int32, [c_int32, c_int64, c_void_p, c_void_p, c_void_p,
                                     c_int32, c_void_p, POINTER(c_void_p)]),
+    "sptrsv_autotune_cache_clear": (None, []),
     "sptrsv_transform": (c_int32, [c_void_p, POINTER(TransformParams), c_void_p]),
     "sptrsv_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "sptrsv_check": (c_int32, [c_void_p, c_void_p]),
@@ -151,6 +153,10 @@ def _check(code: int, what: str) -> None:
 
 
 # --- C entry points, same names -------------------------------------------
+
+def sptrsv_autotune_cache_clear() -> None:
+    load().sptrsv_autotune_cache_clear()
+
 
 def sptrsv_default_params() -> TransformParams:
     prm = TransformParams()

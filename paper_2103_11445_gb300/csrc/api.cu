@@ -7,6 +7,8 @@
 #include <cmath>
 #include <functional>
 #include <map>
+#include <mutex>
+#include <tuple>
 #include <utility>
 
 #include "plan.cuh"
@@ -597,7 +599,64 @@ sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t 
 // free) at three launch shapes; stage 2 sweeps the launch shape of the two
 // best (lanes, mode) pairs; stage 3 the polling back-off of the sync-free
 // kernel.  Trials of long solves use fewer repetitions.
+// Autotuning results are kept per process, keyed by what decides them: the
+// device, the plan's shape (rows, entries, level sizes, the chosen segments,
+// terms of the rewritten structure) and every request that constrains the
+// search.  A plan with the same key takes the cached launch without timing.
+struct TuneKey {
+    int device;
+    int32_t n, precision, nrhs_hint, lanes, block, grid, runs, backoff;
+    int64_t nnz, nnz_x, nnz_b;
+    uint64_t shape;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(device, n, precision, nrhs_hint, lanes, block, grid, runs, backoff, nnz,
+                        nnz_x, nnz_b, shape) <
+               std::tie(o.device, o.n, o.precision, o.nrhs_hint, o.lanes, o.block, o.grid,
+                        o.runs, o.backoff, o.nnz, o.nnz_x, o.nnz_b, o.shape);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, SolveConfig> g_tune_cache;
+
+TuneKey tune_key(sptrsv_plan_t p) {
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over level sizes and segments
+    auto mix = [&](uint64_t v) {
+        for (int b = 0; b < 8; ++b) {
+            h ^= (v >> (8 * b)) & 0xff;
+            h *= 1099511628211ull;
+        }
+    };
+    for (int32_t v : p->h_level_ptr) mix((uint64_t)(uint32_t)v);
+    for (size_t i = 0; i < p->seg_first.size(); ++i)
+        mix(((uint64_t)(uint32_t)p->seg_first[i] << 32) | (uint32_t)p->seg_depth[i]);
+    const auto &q = p->prm;
+    return TuneKey{p->device, p->n, q.precision, q.nrhs_hint, q.lanes_per_row, q.block_threads,
+                   q.grid_blocks, q.cta_run_rows, q.poll_backoff_ns, p->nnz, p->nnz_x,
+                   p->nnz_b, h};
+}
+
+sptrsv_status_t autotune_search(sptrsv_plan_t p, cudaStream_t s);
+
 sptrsv_status_t autotune(sptrsv_plan_t p, cudaStream_t s) {
+    if (p->n == 0) return SPTRSV_OK;
+    const TuneKey key = tune_key(p);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            p->cfg = it->second;
+            p->tuned_from_cache = true;
+            return apply_config(p, s);
+        }
+    }
+    p->tuned_from_cache = false;
+    CKS(autotune_search(p, s));
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = p->cfg;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t autotune_search(sptrsv_plan_t p, cudaStream_t s) {
     const int32_t n = p->n;
     if (n == 0) return SPTRSV_OK;
     const bool f32 = p->prm.precision == SPTRSV_F32_IR;
@@ -1089,6 +1148,11 @@ sptrsv_status_t sptrsv_transform(sptrsv_plan_t p, const sptrsv_transform_params_
     return SPTRSV_OK;
 }
 
+void sptrsv_autotune_cache_clear(void) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache.clear();
+}
+
 sptrsv_status_t sptrsv_solve(sptrsv_plan_t p, const double *d_b, double *d_x, int32_t nrhs,
                              sptrsv_stream_t stream) {
     if (!p) return SPTRSV_ERR_INVALID_ARG;
@@ -1136,6 +1200,7 @@ sptrsv_status_t sptrsv_get_info(sptrsv_plan_t p, sptrsv_info_t *o) {
     o->analyze_ms = p->analyze_ms;
     o->transform_ms = p->transform_ms;
     o->op = p->op;
+    o->tuned_from_cache = p->tuned_from_cache ? 1 : 0;
     if (p->status.p) {
         DevStatus h;
         if (cudaMemcpy(&h, p->status.p, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess)

@@ -128,6 +128,7 @@ struct sptrsv_plan_s {
     sptrsv_status_t latched = SPTRSV_OK;
     sptrsv_mlp_t costmodel = nullptr;  // not owned
     int32_t chosen_depth = -1;         // depth picked by the cost model (-1: none)
+    bool tuned_from_cache = false;     // the last autotuning reused a cached launch
     // profiling: events around the main solve kernel of the last solve
     bool profiling = false;
     cudaEvent_t prof_ev[2] = {nullptr, nullptr};

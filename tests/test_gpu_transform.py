@@ -176,3 +176,26 @@ def test_fill_cap_stops_merging():
     first, depth = P.segments()
     assert list(zip(first, depth)) == tr.segments
     assert max(r.fill for r in tr.rows.values()) <= 12
+
+
+def test_autotune_cache_reuses_the_launch_for_the_same_shape():
+    from paper_2103_11445_gb300 import binding as B
+    B.sptrsv_autotune_cache_clear()
+    A = mg.stencil3d(24, seed=8)
+    P = plan_for(A, select_mode=3, depth=2)          # SOLVE_AUTO: timed
+    i1 = P.info()
+    assert i1["tuned_from_cache"] == 0
+    Q = plan_for(A, select_mode=3, depth=2)          # same shape: cached
+    i2 = Q.info()
+    assert i2["tuned_from_cache"] == 1
+    for k in ("solve_mode", "lanes_per_row", "block_threads", "grid_blocks", "cta_run_rows",
+              "poll_backoff_ns"):
+        assert i1[k] == i2[k], k
+    assert i2["transform_ms"] < i1["transform_ms"]
+    b = mg.rhs_uniform(A.n, seed=3)
+    assert_close_to_oracle(A, gpu_solve(Q, b), b, TOL64)
+    P.transform(select_mode=3, depth=3)              # another shape: timed again
+    assert P.info()["tuned_from_cache"] == 0
+    B.sptrsv_autotune_cache_clear()
+    P.transform(select_mode=3, depth=2)
+    assert P.info()["tuned_from_cache"] == 0
