@@ -62,7 +62,7 @@ typedef enum {
     SPTRSV_ERR_CUDA = 7,          /* a CUDA runtime call failed */
     SPTRSV_ERR_TIMEOUT = 8,       /* a bounded device wait gave up */
     SPTRSV_ERR_BAD_STATE = 9,     /* call out of order or plan already failed */
-    SPTRSV_ERR_UNSUPPORTED = 10   /* size or mode this build does not handle */
+    SPTRSV_ERR_UNSUPPORTED = 10   /* size or mode the library does not handle */
 } sptrsv_status_t;
 
 typedef struct sptrsv_plan_s *sptrsv_plan_t;    /* opaque, owned by the library */
