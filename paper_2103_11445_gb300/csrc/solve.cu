@@ -196,6 +196,39 @@ __device__ __forceinline__ void keep_in_run(const Ctx &cx, int32_t pos, T v) {
 }
 
 // One right-hand side; L lanes per row (compile time).
+// U consecutive steps of one lane's entries: U entry loads, then U x (or b)
+// loads in flight together, then the terms already computed and, last, the
+// late arrivals, each one dependent FMA on a sum that starts at b_i.
+template <typename T, int U, bool SF>
+__device__ __forceinline__ void row_batch(const int32_t *cp, const T *vp, int64_t stride, int step,
+                                          T *out, const Ctx &cx, T &acc, bool &bail) {
+    int32_t cc[U];
+    T vv[U], xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        cc[u] = __ldg(cp + (int64_t)(step + u) * stride);
+        vv[u] = __ldg(vp + (int64_t)(step + u) * stride);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (cc[u] >= 0) xv[u] = load_x<T, SF>(out + (int64_t)cc[u] * cx.ld);
+        else xv[u] = other_term<T>(cx, cc[u], out, 0);
+    }
+    bool pend[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        pend[u] = SF && cc[u] >= 0 && Bits<T>::of(xv[u]) == Sentinel<T>::bits;
+        if (!pend[u]) acc = fma(-vv[u], xv[u], acc);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+        if (pend[u])
+            acc = fma(-vv[u],
+                      wait_x<T>(out + (int64_t)cc[u] * cx.ld, cx.st, cx.timeout_ns, cx.backoff_ns,
+                                bail),
+                      acc);
+}
+
 template <typename T, int L, bool SF>
 __device__ __forceinline__ bool chunk_one(const SolveData<T> &sd, int32_t c, T *out,
                                           const Ctx &cx) {
@@ -218,32 +251,11 @@ __device__ __forceinline__ bool chunk_one(const SolveData<T> &sd, int32_t c, T *
         const int32_t *cp = sd.ecol + mt.w + k * L + s;
         const T *vp = sd.eval + mt.w + k * L + s;
         int step = 0;
-        constexpr int U = 4;
-        for (; step + U <= mt.z; step += U) {
-            int32_t cc[U];
-            T vv[U], xv[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                cc[u] = __ldg(cp + (int64_t)(step + u) * stride);
-                vv[u] = __ldg(vp + (int64_t)(step + u) * stride);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (cc[u] >= 0) xv[u] = load_x<T, SF>(out + (int64_t)cc[u] * cx.ld);
-                else xv[u] = other_term<T>(cx, cc[u], out, 0);
-            }
-            // the row's sum runs from b_i down: terms already computed first,
-            // late arrivals last, so that each costs one dependent FMA
-            bool pend[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                pend[u] = SF && cc[u] >= 0 && Bits<T>::of(xv[u]) == Sentinel<T>::bits;
-                if (!pend[u]) acc = fma(-vv[u], xv[u], acc);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (pend[u])
-                    acc = fma(-vv[u], wait_x<T>(out + (int64_t)cc[u] * cx.ld, cx.st, cx.timeout_ns, cx.backoff_ns, bail), acc);
+        for (; step + 4 <= mt.z; step += 4)
+            row_batch<T, 4, SF>(cp, vp, stride, step, out, cx, acc, bail);
+        if (step + 2 <= mt.z) {
+            row_batch<T, 2, SF>(cp, vp, stride, step, out, cx, acc, bail);
+            step += 2;
         }
         for (; step < mt.z; ++step) {
             const int32_t cc = __ldg(cp + (int64_t)step * stride);
