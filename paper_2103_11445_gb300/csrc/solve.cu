@@ -253,9 +253,11 @@ __device__ __forceinline__ bool chunk_one(const SolveData<T> &sd, int32_t c, T *
         int step = 0;
         for (; step + 4 <= mt.z; step += 4)
             row_batch<T, 4, SF>(cp, vp, stride, step, out, cx, acc, bail);
-        if (step + 2 <= mt.z) {
-            row_batch<T, 2, SF>(cp, vp, stride, step, out, cx, acc, bail);
-            step += 2;
+        switch (mt.z - step) {  // the remainder as one batch of its exact size
+        case 3: row_batch<T, 3, SF>(cp, vp, stride, step, out, cx, acc, bail); step += 3; break;
+        case 2: row_batch<T, 2, SF>(cp, vp, stride, step, out, cx, acc, bail); step += 2; break;
+        case 1: row_batch<T, 1, SF>(cp, vp, stride, step, out, cx, acc, bail); step += 1; break;
+        default: break;
         }
         for (; step < mt.z; ++step) {
             const int32_t cc = __ldg(cp + (int64_t)step * stride);
