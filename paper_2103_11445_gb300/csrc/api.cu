@@ -105,7 +105,7 @@ std::vector<std::pair<int32_t, int32_t>> select_segments(
 
 // Evaluates candidate rewrites (level l lifted by r levels) on the device,
 // in batches, caching the results.
-struct FillOracle {
+struct FillQuery {
     sptrsv_plan_t p;
     cudaStream_t s;
     int cap;
@@ -179,7 +179,7 @@ sptrsv_status_t compute_segments(sptrsv_plan_t p, int64_t tau, int32_t d_max, do
     const int32_t nlev = p->nlev;
     std::vector<int64_t> rows(nlev);
     for (int32_t l = 0; l < nlev; ++l) rows[l] = p->h_level_ptr[l + 1] - p->h_level_ptr[l];
-    FillOracle fo{p, s, p->prm.max_row_fill};
+    FillQuery fo{p, s, p->prm.max_row_fill, {}};
     // speculative batch: the uncut path plus every first step after a cut
     std::vector<std::pair<int32_t, int32_t>> qs;
     fo.optimistic_from(0, rows, tau, d_max, qs);
