@@ -169,3 +169,19 @@ def test_wrong_triangle_and_bad_op_are_rejected():
     with pytest.raises(B.SptrsvError) as ei:
         B.Plan(L.n, L.row_ptr, L.col, L.val, op=7)
     assert ei.value.code == 1
+
+
+def test_upper_operator_with_column_hint():
+    """U x = b with a structure laid out for 8 columns, solved with 5."""
+    import torch
+    from paper_2103_11445_gb300 import binding as B
+    L = mg.thin_tail(8000, seed=91)
+    U = mg.transposed(L)
+    P = B.Plan(U.n, U.row_ptr, U.col, U.val, op=1)
+    P.transform(select_mode=3, depth=2, solve_mode=2, nrhs_hint=8)
+    assert P.info()["lanes_per_row"] == 8
+    b = mg.rhs_uniform(U.n, nrhs=5, seed=92)
+    x = P.solve(torch.as_tensor(b, device="cuda"))
+    P.check()
+    assert oracle.relerr(x.cpu().numpy(), oracle.solve_op(U, b, 1)) <= TOL64
+    P.close()

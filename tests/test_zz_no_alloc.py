@@ -67,3 +67,20 @@ def test_noalloc_rejects_oversize_and_wrong_precision():
     P.check()
     assert oracle.relerr(xx.cpu().numpy(), oracle.forward_subst(A, b_np)) <= TOL64
     P.close()
+
+
+def test_noalloc_on_a_transposed_operator():
+    """L^T x = b through the no-allocation solve: the refinement's residual
+    runs on the mirrored triangle with the mirrored index map."""
+    import torch
+    from paper_2103_11445_gb300 import binding as B
+    L = mg.thin_tail(8000, seed=91)
+    Q = B.Plan(L.n, L.row_ptr, L.col, L.val, op=B.OP_LOWER_TRANS)
+    Q.transform(select_mode=1, solve_mode=2, precision=1)
+    b1 = mg.rhs_uniform(L.n, nrhs=2, seed=93)
+    bt = torch.as_tensor(b1, device="cuda")
+    xt = torch.empty_like(bt)
+    B.sptrsv_solve_ir_noalloc(Q.handle, bt.data_ptr(), xt.data_ptr(), 2, 0)
+    Q.check()
+    assert oracle.relerr(xt.cpu().numpy(), oracle.solve_op(L, b1, oracle.OP_LOWER_TRANS)) <= TOL64
+    Q.close()
