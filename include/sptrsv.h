@@ -205,10 +205,11 @@ SPTRSV_API sptrsv_status_t sptrsv_analyze_ex(int32_t n, int64_t nnz, const int32
 SPTRSV_API sptrsv_status_t sptrsv_transform(sptrsv_plan_t p, const sptrsv_transform_params_t *prm,
                                  sptrsv_stream_t stream);
 
-/* x = L^{-1} b for nrhs right-hand sides (1..32 per launch; more are solved
- * 32 columns at a time), row-major [n][nrhs] device buffers.  x must not
- * overlap b.  Asynchronous.  In F32_IR precision the solve runs on FP32 copies
- * of the values and refines with FP64 residuals of the original L. */
+/* x = op(A)^{-1} b (L^{-1} b for sptrsv_analyze's plans) for nrhs right-hand
+ * sides (1..32 per launch; more are solved 32 columns at a time), row-major
+ * [n][nrhs] device buffers.  x must not overlap b.  Asynchronous.  In F32_IR
+ * precision the solve runs on FP32 copies of the values and refines with
+ * FP64 residuals of the original matrix. */
 SPTRSV_API sptrsv_status_t sptrsv_solve(sptrsv_plan_t p, const double *d_b, double *d_x,
                              int32_t nrhs, sptrsv_stream_t stream);
 
@@ -226,7 +227,9 @@ SPTRSV_API void sptrsv_plan_destroy(sptrsv_plan_t p);
 
 /* Analysis results (for inspection and tests), copied to device buffers:
  * level int32[n], level_ptr int32[nlev+1], perm int32[n] (rows ordered by
- * level, ascending row index inside a level).  Any pointer may be NULL. */
+ * level, ascending row index inside a level; descending for an upper or
+ * transposed-lower operator, whose mirrored triangle was analysed -- see
+ * sptrsv_analyze_ex).  Any pointer may be NULL. */
 SPTRSV_API sptrsv_status_t sptrsv_get_levels(sptrsv_plan_t p, int32_t *d_level,
                                   int32_t *d_level_ptr, int32_t *d_perm,
                                   sptrsv_stream_t stream);
