@@ -248,6 +248,23 @@ def transposed(A: CSR) -> CSR:
                np.ascontiguousarray(A.val[order]))
 
 
+def symmetric_from_lower(L: CSR) -> CSR:
+    """The symmetric matrix whose lower triangle (diagonal included) is L:
+    L's entries plus the mirror image of its off-diagonal ones, CSR with
+    ascending columns (an input rearrangement, no arithmetic on values)."""
+    rows = np.repeat(np.arange(L.n, dtype=np.int64), np.diff(L.row_ptr))
+    off = L.col != rows
+    r = np.concatenate([rows, L.col[off].astype(np.int64)])
+    c = np.concatenate([L.col.astype(np.int64), rows[off]])
+    v = np.concatenate([L.val, L.val[off]])
+    order = np.lexsort((c, r))
+    cnt = np.bincount(r, minlength=L.n)
+    ptr = np.zeros(L.n + 1, np.int64)
+    np.cumsum(cnt, out=ptr[1:])
+    return CSR(L.n, ptr.astype(np.int32), c[order].astype(np.int32),
+               np.ascontiguousarray(v[order]))
+
+
 def rhs_uniform(n: int, nrhs: int = 1, seed: int = 7) -> np.ndarray:
     """b ~ U[-1, 1], row-major [n, nrhs] (shape [n] when nrhs == 1)."""
     rng = np.random.default_rng(seed)

@@ -19,7 +19,10 @@ Contents (each function cites the passage of the paper it follows):
 * ``rewrite``        equation rewriting of one row (Sec. III, Figs. 2-3) and
   the thin-level selection heuristic -- Python, ``rewrite.py``;
 * ``mlp``            FP64 forward/backward/Adam of the 3-layer cost-model
-  network -- numpy, ``mlp.py``.
+  network -- numpy, ``mlp.py``;
+* ``pcg``            preconditioned conjugate gradients with the symmetric
+  Gauss-Seidel preconditioner (two triangular solves per step) -- numpy and
+  the substitutions above, ``pcg.py``.
 
 Parity status: every function above is pinned by tests against closed
 forms, exact rational arithmetic, library routines or brute force; the
