@@ -49,12 +49,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--side", type=int, default=128, help="grid side of the 3D stencil")
-    ap.add_argument("--workload", choices=["stencil3d", "thin_tail", "batch256"],
+    ap.add_argument("--workload", choices=["stencil3d", "thin_tail", "batch256", "pcg"],
                     default="stencil3d",
                     help="stencil3d: the 3D 7-point lower triangle (default); thin_tail: the "
                          "1M-row random-banded matrix with a near-serial 50k-row tail; "
                          "batch256: 256 uneven matrices with 1-32 right-hand sides each, FP32 "
-                         "values + FP64 refinement, one graph-replayed launch")
+                         "values + FP64 refinement, one graph-replayed launch; pcg: conjugate "
+                         "gradients on the full symmetric 3D 7-point matrix with the symmetric "
+                         "Gauss-Seidel preconditioner (two triangular solves per step), a step "
+                         "one solve to relative residual 1e-8")
     ap.add_argument("--depths", default="1,2,3,4,6",
                     help="fixed rewrite depths tried besides heuristic H")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -236,6 +239,8 @@ def run_reference(args, world, rank):
     oracle.build()
     if args.workload == "batch256":
         return run_reference_batch(args)
+    if args.workload == "pcg":
+        return run_reference_pcg(args)
     A, b = workload(args.side, args.workload)
     for _ in range(max(args.warmup, 0)):
         oracle.forward_subst(A, b)
@@ -749,6 +754,217 @@ def run_batch(args, world, rank):
     return 0
 
 
+PCG_METRIC = "PCG-SGS iterations/s (solves to |r|/|b| <= 1e-8, start-up included), FP64"
+PCG_RTOL = 1e-8
+
+
+def pcg_workload(side: int):
+    import matgen as mg
+    A = mg.symmetric_from_lower(mg.stencil3d(side, seed=2000))
+    return A, mg.rhs_uniform(A.n, seed=2001)
+
+
+def pcg_name(side: int, A) -> str:
+    return (f"pcg_stencil3d_{side} (full symmetric 3D 7-point Laplacian, n={A.n}, nnz={A.nnz}, "
+            f"diag 6+U[0,0.1], b~U[-1,1], x0=0, rtol {PCG_RTOL:g})")
+
+
+def pcg_bytes_per_step(n: int, nnz_a: int, nnz_l: int) -> dict:
+    """Algorithmic bytes of one PCG step (the vectors and matrices each
+    kernel must read or write once): A p; two triangular solves; D y; the
+    dot products (p, q), (r, r), (r, z); x, r and p updates."""
+    spmv = 12 * nnz_a + 4 * (n + 1) + 16 * n
+    trsv = b_alg(n, nnz_l)
+    return dict(spmv=spmv, trsv=trsv, total=spmv + 2 * trsv + 24 * n + 48 * n + 48 * n + 24 * n)
+
+
+def run_pcg(args, world, rank):
+    """Preconditioned CG on the symmetric 3D 7-point matrix: every step runs
+    A p, two triangular solves of the lower triangle (forward, transposed)
+    through the rewritten plans, and the vector updates, all in the library's
+    kernels.  value = solves per second over all ranks."""
+    import numpy as np
+    import torch
+    from paper_2103_11445_gb300 import binding as Bd
+    import oracle
+    from oracle import pcg as opcg
+    dev = torch.device("cuda", torch.cuda.current_device())
+    A, b_np = pcg_workload(args.side)
+    n = A.n
+    rp, col, val = (torch.as_tensor(a, device=dev) for a in (A.row_ptr, A.col, A.val))
+    b = torch.as_tensor(b_np, device=dev)
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+    sel = dict(select_mode=Bd.SELECT_FIXED, depth=2)
+    t0 = time.perf_counter()
+    G = Bd.PCG(n, rp, col, val, lower=sel, upper=sel)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    ilo, iup = G.plan_info()
+    lo_h, up_h = Bd.sptrsv_pcg_get_plans(G.handle)
+
+    def solve_once():
+        x.zero_()
+        return G.solve(b, x, rtol=PCG_RTOL, max_iter=2000)
+
+    for _ in range(args.warmup):
+        solve_once()
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    Bd.sptrsv_set_profiling(lo_h, True)
+    Bd.sptrsv_set_profiling(up_h, True)
+    step_ms, kern_lo, kern_up, iters = [], [], [], []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, it, rel = solve_once()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        iters.append(it)
+        kern_lo.append(Bd.sptrsv_last_kernel_ms(lo_h))
+        kern_up.append(Bd.sptrsv_last_kernel_ms(up_h))
+    Bd.sptrsv_set_profiling(lo_h, False)
+    Bd.sptrsv_set_profiling(up_h, False)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = max_over_ranks(world, statistics.mean(step_ms))
+    it = iters[-1]
+    value = world * it / (ms * 1e-3)
+    xg = x.cpu().numpy()
+    import scipy.sparse as sps
+    As = sps.csr_matrix((A.val, A.col, A.row_ptr), shape=(n, n))
+    true_rel = float(np.linalg.norm(b_np - As @ xg) / np.linalg.norm(b_np))
+    # the same iteration with the plain level-set plans (no rewriting)
+    G0 = Bd.PCG(n, rp, col, val, lower=dict(select_mode=Bd.SELECT_NONE),
+                upper=dict(select_mode=Bd.SELECT_NONE))
+    plain = []
+    for k in range(3 + max(2, args.steps // 4)):
+        x0 = torch.zeros_like(b)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, it0, _ = G0.solve(b, x0, rtol=PCG_RTOL, max_iter=2000)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= 3:
+            plain.append(e0.elapsed_time(e1))
+    G0.close()
+    # end to end: b from pinned host memory in, x out, every step
+    hb = torch.from_numpy(b_np.copy()).pin_memory()
+    hx = torch.empty_like(hb).pin_memory()
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.copy_(hb, non_blocking=True)
+        solve_once()
+        hx.copy_(x, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e = world * it / (max_over_ranks(world, statistics.mean(e2e_ms)) * 1e-3)
+    # the dominant kernel: the triangular solves, timed live on their stream
+    kms = statistics.mean(kern_lo + kern_up)
+    byt = pcg_bytes_per_step(n, A.nnz, ilo["nnz"])
+    peak, peak_kind = peaks()
+    ach = byt["trsv"] / (kms * 1e-3) / 1e9
+    line = None
+    if rank == 0:
+        # CPU oracle: one full solve of the same system (about half a minute
+        # on one core); its step count and solution double as a parity check
+        t1 = time.perf_counter()
+        x_cpu, it_cpu, rel_cpu = opcg.pcg(A, b_np, np.zeros(n), rtol=PCG_RTOL, max_iter=2000)
+        cpu_s = time.perf_counter() - t1
+        n_launch = 11 + 13 * (it - 1) + 6
+        line = {
+            "metric": PCG_METRIC, "value": round(value, 3), "unit": "iterations/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": pcg_name(args.side, A), "pcg_iterations": it,
+                       "oracle_iterations": it_cpu, "solves_per_s": round(world / (ms * 1e-3), 4),
+                       "final_relres": rel, "true_relres": true_rel,
+                       "ms_per_iteration": round(ms / max(it, 1), 4),
+                       "plans": "D+L as L and as L^T, fixed depth 2, autotuned",
+                       "nlev": ilo["nlev"], "nlev_new": [ilo["nlev_new"], iup["nlev_new"]],
+                       "plain_plans_ms_per_solve": round(statistics.mean(plain), 3),
+                       "plain_plans_iterations": it0,
+                       "trsv_kernel_ms": [round(statistics.mean(kern_lo), 4),
+                                          round(statistics.mean(kern_up), 4)],
+                       "trsv_share_of_step": round(it * (statistics.mean(kern_lo) +
+                                                         statistics.mean(kern_up)) / ms, 3),
+                       "b_alg_bytes_per_iteration": byt["total"],
+                       "setup_ms": round(setup_ms, 1),
+                       "l2": "not flushed: the working set (A, two solve structures, eight "
+                             "vectors) is several times the 129 MB L2",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": round(ach, 2), "peak": peak,
+                         "unit": "GB/s", "frac": round(ach / peak, 4),
+                         "peak_kind": f"{peak_kind} copy bandwidth",
+                         "kernel": "the two triangular-solve kernels of a step (B_alg of D+L "
+                                   "per solve / their mean duration, CUDA events recorded by "
+                                   "the library on its solve stream during the timed steps)",
+                         "traffic": None},
+            "e2e": {"value": round(e2e, 4), "unit": "iterations/s", "h2d_bytes_per_step": 8 * n,
+                    "d2h_bytes_per_step": 8 * n + 8 * (it + 1)},
+            "gpu_launches": n_launch * args.steps,
+            "clocks": clk,
+            "cpu_baseline": {"value": round(it_cpu / cpu_s, 4), "unit": "iterations/s",
+                             "cores": 1, "kind": "oracle",
+                             "sample": f"one full oracle PCG solve (oracle/pcg.py) of the same "
+                                       f"system, {it_cpu} steps in {cpu_s:.1f} s; 1 of "
+                                       f"{len(os.sched_getaffinity(0))} host cores"},
+            "relerr_vs_oracle": oracle.relerr(xg, x_cpu),
+        }
+        print(json.dumps(line), flush=True)
+    G.close()
+    return 0
+
+
+def run_reference_pcg(args, sample_steps: int = 8):
+    """The oracle's PCG on the pcg workload; each bench step is a bounded
+    sample: PCG from x0 = 0 for `sample_steps` steps (start-up included, as in
+    the GPU arm's solves), so the value is iterations per second."""
+    import numpy as np
+    from oracle import pcg as opcg
+    A, b_np = pcg_workload(args.side)
+    for _ in range(max(args.warmup, 0)):
+        opcg.pcg(A, b_np, np.zeros(A.n), rtol=0.0, max_iter=sample_steps)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        opcg.pcg(A, b_np, np.zeros(A.n), rtol=0.0, max_iter=sample_steps)
+        times.append(time.perf_counter() - t0)
+    ms = statistics.mean(times) * 1e3
+    val = sample_steps / (ms * 1e-3)
+    line = {
+        "impl": "reference", "metric": PCG_METRIC, "value": round(val, 4),
+        "unit": "iterations/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": pcg_name(args.side, A)},
+        "cpu_baseline": {"value": round(val, 4), "unit": "iterations/s", "cores": 1,
+                         "kind": "oracle",
+                         "sample": f"{sample_steps} oracle PCG steps from x0 = 0 per bench "
+                                   f"step (start-up r0 = b - A x0, z0 = M^-1 r0 included), "
+                                   f"1 of {len(os.sched_getaffinity(0))} host cores"},
+        "e2e": {"value": round(val, 4), "unit": "iterations/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -758,6 +974,8 @@ def main():
         rc = run_profile(args)
     elif args.workload == "batch256":
         rc = run_batch(args, world, rank)
+    elif args.workload == "pcg":
+        rc = run_pcg(args, world, rank)
     else:
         rc = run_ours(args, world, rank, local)
     if world > 1:

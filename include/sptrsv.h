@@ -68,6 +68,7 @@ typedef enum {
 typedef struct sptrsv_plan_s *sptrsv_plan_t;    /* opaque, owned by the library */
 typedef struct sptrsv_batch_s *sptrsv_batch_t;  /* opaque, owned by the library */
 typedef struct sptrsv_mlp_s *sptrsv_mlp_t;      /* opaque, owned by the library */
+typedef struct sptrsv_pcg_s *sptrsv_pcg_t;      /* opaque, owned by the library */
 typedef void *sptrsv_stream_t;                  /* cudaStream_t */
 
 /* Row selection for the rewriting (Sec. III; the paper chooses rows by
@@ -332,6 +333,56 @@ SPTRSV_API sptrsv_status_t sptrsv_batch_get_info(sptrsv_batch_t batch, int32_t *
                                                  int32_t *h_converged, int32_t *h_cta_count,
                                                  int32_t *h_graph);
 SPTRSV_API void sptrsv_batch_destroy(sptrsv_batch_t batch);
+
+/* Preconditioned conjugate gradients with the symmetric Gauss-Seidel
+ * preconditioner -- a consumer of the triangular solve (Sec. I names the
+ * iterative solvers that spend their time in SpTRSV as the method's users).
+ * For an SPD matrix A = L + D + L^T the preconditioner is
+ * M = (D + L) D^{-1} (D + L)^T, applied each step as two triangular solves:
+ * (D + L) y = r and (D + L)^T z = D y.
+ *
+ * sptrsv_pcg_create: A is the FULL symmetric matrix in device CSR
+ * (row_ptr[n+1], col[nnz], val[nnz], int32 / FP64, columns ascending per
+ * row, diagonal stored, n >= 1, nnz >= 1); the library copies it, so the
+ * caller's arrays may be freed afterwards.  The call extracts D + L on the
+ * device and builds two plans of it, one analysed as SPTRSV_OP_LOWER and one
+ * as SPTRSV_OP_LOWER_TRANS, transformed with prm_lower and prm_upper (NULL:
+ * sptrsv_default_params).  The PCG object owns both plans; synchronises
+ * `stream`.  The library does not check that A is symmetric or positive
+ * definite; the iteration has no meaning otherwise.
+ * Errors: SPTRSV_ERR_INVALID_ARG (null pointer, sizes), SPTRSV_ERR_UNSORTED
+ * (row_ptr not monotone inside [0, nnz]), SPTRSV_ERR_NOT_LOWER (a column
+ * outside [0, n)), the analysis codes of D + L (unsorted columns, missing or
+ * zero diagonal) and the transforms', SPTRSV_ERR_OOM, SPTRSV_ERR_CUDA.
+ *
+ * sptrsv_pcg_get_plans: the two plans (borrowed: valid until
+ * sptrsv_pcg_destroy) for sptrsv_get_info, profiling or a new transform.
+ *
+ * sptrsv_pcg_solve: x (device, FP64, n) holds the initial guess on entry and
+ * the iterate on return; b (device, FP64, n) is not modified.  Steps until
+ * |r|_2 <= rtol |b|_2 for the recursively updated residual r, or max_iter
+ * steps; *h_iters gets the steps taken and *h_relres |r|_2 / |b|_2 at the
+ * end (either pointer may be NULL).  b = 0 gives x = 0 and no step.  Reads
+ * the residual norm to the host once per step, so the call synchronises
+ * `stream` every step and returns after the solve is complete.  Dot products
+ * reduce in a fixed order; a synchronisation-free triangular solve adds a
+ * row's terms partly in the order they become ready, so two runs can differ
+ * in the last bits (and, near the tolerance, by one step).  A latched
+ * error of either plan's solves (e.g. SPTRSV_ERR_TIMEOUT) is returned at the
+ * end; calls on one PCG object must not overlap.  Errors:
+ * SPTRSV_ERR_INVALID_ARG (null object, b or x, max_iter < 0, rtol < 0 or
+ * NaN), SPTRSV_ERR_CUDA, and the solves'. */
+SPTRSV_API sptrsv_status_t sptrsv_pcg_create(int32_t n, int64_t nnz, const int32_t *d_row_ptr,
+                                             const int32_t *d_col, const double *d_val,
+                                             const sptrsv_transform_params_t *prm_lower,
+                                             const sptrsv_transform_params_t *prm_upper,
+                                             sptrsv_stream_t stream, sptrsv_pcg_t *out);
+SPTRSV_API sptrsv_status_t sptrsv_pcg_get_plans(sptrsv_pcg_t pcg, sptrsv_plan_t *lower,
+                                                sptrsv_plan_t *upper);
+SPTRSV_API sptrsv_status_t sptrsv_pcg_solve(sptrsv_pcg_t pcg, const double *d_b, double *d_x,
+                                            double rtol, int32_t max_iter, int32_t *h_iters,
+                                            double *h_relres, sptrsv_stream_t stream);
+SPTRSV_API void sptrsv_pcg_destroy(sptrsv_pcg_t pcg);
 
 /* The FP32 + FP64-refinement solve without any device allocation.  The
  * paper has no counterpart: this exists for callers that cannot call

@@ -111,6 +111,12 @@ _SIGS = {
     "sptrsv_set_profiling": (c_int32, [c_void_p, c_int32]),
     "sptrsv_solve_ir_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "sptrsv_last_kernel_ms": (c_int32, [c_void_p, POINTER(ctypes.c_float)]),
+    "sptrsv_pcg_create": (c_int32, [c_int32, c_int64, c_void_p, c_void_p, c_void_p,
+                                    c_void_p, c_void_p, c_void_p, POINTER(c_void_p)]),
+    "sptrsv_pcg_get_plans": (c_int32, [c_void_p, POINTER(c_void_p), POINTER(c_void_p)]),
+    "sptrsv_pcg_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_double, c_int32,
+                                   POINTER(c_int32), POINTER(c_double), c_void_p]),
+    "sptrsv_pcg_destroy": (None, [c_void_p]),
 }
 
 
@@ -344,6 +350,37 @@ def sptrsv_batch_destroy(batch: int) -> None:
         load().sptrsv_batch_destroy(batch)
 
 
+def sptrsv_pcg_create(n: int, nnz: int, d_row_ptr: int, d_col: int, d_val: int,
+                      prm_lower: TransformParams | None = None,
+                      prm_upper: TransformParams | None = None, stream: int = 0) -> int:
+    out = c_void_p()
+    _check(load().sptrsv_pcg_create(n, nnz, d_row_ptr, d_col, d_val,
+                                    byref(prm_lower) if prm_lower is not None else None,
+                                    byref(prm_upper) if prm_upper is not None else None,
+                                    stream, byref(out)), "sptrsv_pcg_create")
+    return out.value
+
+
+def sptrsv_pcg_get_plans(pcg: int):
+    lo, up = c_void_p(), c_void_p()
+    _check(load().sptrsv_pcg_get_plans(pcg, byref(lo), byref(up)), "sptrsv_pcg_get_plans")
+    return lo.value, up.value
+
+
+def sptrsv_pcg_solve(pcg: int, d_b: int, d_x: int, rtol: float, max_iter: int,
+                     stream: int = 0):
+    """(iterations, final relative residual norm)."""
+    it, rel = c_int32(), c_double()
+    _check(load().sptrsv_pcg_solve(pcg, d_b, d_x, rtol, max_iter, byref(it), byref(rel),
+                                   stream), "sptrsv_pcg_solve")
+    return it.value, rel.value
+
+
+def sptrsv_pcg_destroy(pcg: int) -> None:
+    if pcg:
+        load().sptrsv_pcg_destroy(pcg)
+
+
 # --- torch convenience wrapper ---------------------------------------------
 
 def _stream_handle(stream) -> int:
@@ -443,6 +480,69 @@ class Plan:
     def close(self) -> None:
         if self._handle:
             sptrsv_plan_destroy(self._handle)
+            self._handle = 0
+
+    def __del__(self):  # pragma: no cover - interpreter shutdown order
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PCG:
+    """Owns a preconditioned-CG object (symmetric Gauss-Seidel) built from a
+    full symmetric CSR matrix in torch tensors or numpy arrays; ``lower`` and
+    ``upper`` are dicts of transform parameters for its two triangular plans
+    (None: the library defaults)."""
+
+    def __init__(self, n: int, row_ptr, col, val, lower=None, upper=None, stream=None):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+
+        def t(a, dt):
+            return torch.as_tensor(a, dtype=dt, device=dev).contiguous()
+
+        def prm(kw):
+            if kw is None:
+                return None
+            p = sptrsv_default_params()
+            for k, v in kw.items():
+                if not hasattr(p, k):
+                    raise TypeError(f"unknown transform parameter {k}")
+                setattr(p, k, v)
+            return p
+
+        self.n = int(n)
+        rp, c, v = t(row_ptr, torch.int32), t(col, torch.int32), t(val, torch.float64)
+        self._handle = 0
+        self._handle = sptrsv_pcg_create(self.n, int(c.numel()), rp.data_ptr(), c.data_ptr(),
+                                         v.data_ptr(), prm(lower), prm(upper),
+                                         _stream_handle(stream))
+
+    @property
+    def handle(self) -> int:
+        return self._handle
+
+    def plan_info(self):
+        """(info of the D + L plan, info of the (D + L)^T plan)."""
+        lo, up = sptrsv_pcg_get_plans(self._handle)
+        return sptrsv_get_info(lo).as_dict(), sptrsv_get_info(up).as_dict()
+
+    def solve(self, b, x=None, rtol: float = 1e-8, max_iter: int = 1000, stream=None):
+        """(x, iterations, relative residual); x (if given) is the initial
+        guess and is overwritten, else the iteration starts from zero."""
+        import torch
+        if b.dtype != torch.float64 or not b.is_cuda or not b.is_contiguous() or b.dim() != 1:
+            raise TypeError("b must be a contiguous 1-D float64 CUDA tensor")
+        if x is None:
+            x = torch.zeros_like(b)
+        it, rel = sptrsv_pcg_solve(self._handle, b.data_ptr(), x.data_ptr(), rtol, max_iter,
+                                   _stream_handle(stream))
+        return x, it, rel
+
+    def close(self) -> None:
+        if self._handle:
+            sptrsv_pcg_destroy(self._handle)
             self._handle = 0
 
     def __del__(self):  # pragma: no cover - interpreter shutdown order

@@ -1,0 +1,147 @@
+"""GPU parity of preconditioned conjugate gradients with the symmetric
+Gauss-Seidel preconditioner (sptrsv_pcg_*): every step's two triangular
+solves run through the library's plans of the lower triangle (forward, and
+transposed), compared with the oracle's PCG (oracle/pcg.py) on the same
+inputs -- same iteration counts, iterates equal up to rounding -- and at the
+full 128^3 size with properties that hold at any size (true residual within
+the tolerance, repeatability up to rounding)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import matgen as mg
+import oracle
+from oracle import pcg as opcg
+
+pytestmark = pytest.mark.gpu
+
+
+def scipy_csr(A):
+    return sp.csr_matrix((A.val, A.col, A.row_ptr), shape=(A.n, A.n))
+
+
+def spd_random(n, seed):
+    A = mg.symmetric_from_lower(mg.random_lower(n, seed=seed, density=0.05, diag_min=3.0))
+    assert np.all(np.linalg.eigvalsh(scipy_csr(A).toarray()) > 0)
+    return A
+
+
+MATS = [
+    ("stencil2d_40", lambda: mg.symmetric_from_lower(mg.stencil2d(40))),
+    ("stencil3d_12", lambda: mg.symmetric_from_lower(mg.stencil3d(12, seed=5))),
+    ("random_spd_300", lambda: spd_random(300, 21)),
+]
+PLANS = [
+    ("defaults", None, None),
+    ("fixed_d2_syncfree", dict(select_mode=3, depth=2, solve_mode=2),
+     dict(select_mode=3, depth=2, solve_mode=2)),
+    ("plain_barrier_f32ir", dict(select_mode=0, solve_mode=1, precision=1),
+     dict(select_mode=0, solve_mode=1, precision=1)),
+]
+
+
+@pytest.mark.parametrize("pname,lo,up", PLANS, ids=[p[0] for p in PLANS])
+@pytest.mark.parametrize("name,make", MATS, ids=[m[0] for m in MATS])
+def test_pcg_matches_oracle(name, make, pname, lo, up):
+    import torch
+    from paper_2103_11445_gb300 import binding as B
+    A = make()
+    b = mg.rhs_uniform(A.n, seed=31)
+    x0 = np.random.default_rng(32).uniform(-1, 1, A.n)
+    G = B.PCG(A.n, A.row_ptr, A.col, A.val, lower=lo, upper=up)
+    bt = torch.as_tensor(b, device="cuda")
+    # a fixed number of steps: the iterates agree up to rounding
+    for steps in (1, 5):
+        xr, itr, relr = opcg.pcg(A, b, x0, rtol=0.0, max_iter=steps)
+        x, it, rel = G.solve(bt, torch.as_tensor(x0, device="cuda"), rtol=0.0, max_iter=steps)
+        assert it == itr == steps
+        assert oracle.relerr(x.cpu().numpy(), xr) <= 1e-9, (steps, name, pname)
+        assert abs(rel - relr) <= 1e-8 * max(relr, 1e-300) + 1e-15
+    # to convergence: the same step count (one step of slack for a residual
+    # that lands within rounding of the tolerance) and the same solution
+    xr, itr, relr = opcg.pcg(A, b, np.zeros(A.n), rtol=1e-12, max_iter=2000)
+    x, it, rel = G.solve(bt, rtol=1e-12, max_iter=2000)
+    assert abs(it - itr) <= 1 and rel <= 1e-12 and relr <= 1e-12
+    xs = np.linalg.solve(scipy_csr(A).toarray(), b)
+    assert oracle.relerr(x.cpu().numpy(), xs) <= 1e-8
+    assert oracle.relerr(x.cpu().numpy(), xr) <= 1e-8
+    G.close()
+
+
+def test_pcg_plans_are_the_lower_triangle_in_both_operators():
+    from paper_2103_11445_gb300 import binding as B
+    L = mg.stencil3d(10, seed=2)
+    A = mg.symmetric_from_lower(L)
+    G = B.PCG(A.n, A.row_ptr, A.col, A.val, lower=dict(select_mode=3, depth=2))
+    ilo, iup = G.plan_info()
+    lv, nl = oracle.levels(L)
+    assert ilo["op"] == 0 and iup["op"] == 2
+    assert ilo["nnz"] == iup["nnz"] == L.col.size
+    assert ilo["nlev"] == iup["nlev"] == nl
+    assert ilo["nlev_new"] < nl
+    G.close()
+
+
+def test_pcg_full_stencil3d_128():
+    """The 128^3 7-point Laplacian (n = 2.1M): the true residual, computed
+    by scipy, meets the tolerance; a second solve repeats the first up to
+    rounding (the synchronisation-free solve adds a row's ready terms first,
+    so its last bits can depend on timing)."""
+    import torch
+    from paper_2103_11445_gb300 import binding as B
+    A = mg.symmetric_from_lower(mg.stencil3d(128))
+    b = mg.rhs_uniform(A.n, seed=41)
+    G = B.PCG(A.n, A.row_ptr, A.col, A.val, lower=dict(select_mode=3, depth=2),
+              upper=dict(select_mode=3, depth=2))
+    bt = torch.as_tensor(b, device="cuda")
+    x, it, rel = G.solve(bt, rtol=1e-8, max_iter=1000)
+    assert rel <= 1e-8 and 10 < it < 1000
+    xh = x.cpu().numpy()
+    true_rel = np.linalg.norm(b - scipy_csr(A) @ xh) / np.linalg.norm(b)
+    assert true_rel <= 1.01e-8
+    x2, it2, rel2 = G.solve(bt, rtol=1e-8, max_iter=1000)
+    assert abs(it2 - it) <= 1 and rel2 <= 1e-8
+    assert oracle.relerr(x2.cpu().numpy(), xh) <= 1e-10
+    G.close()
+
+
+def test_pcg_degenerate_inputs():
+    import torch
+    from paper_2103_11445_gb300 import binding as B
+    A = mg.symmetric_from_lower(mg.stencil2d(9))
+    G = B.PCG(A.n, A.row_ptr, A.col, A.val)
+    z = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    x, it, rel = G.solve(z, torch.ones_like(z))          # b = 0: x = 0
+    assert it == 0 and rel == 0.0 and not bool(x.any())
+    xt = np.random.default_rng(3).uniform(-1, 1, A.n)
+    b = torch.as_tensor(scipy_csr(A) @ xt, device="cuda")
+    x, it, rel = G.solve(b, torch.as_tensor(xt, device="cuda"), rtol=1e-10)
+    assert it == 0 and rel <= 1e-10                        # x0 already solves it
+    x, it, rel = G.solve(b, rtol=1e-10, max_iter=0)        # no step allowed
+    assert it == 0 and not bool(x.any()) and rel == pytest.approx(1.0)
+    for kw in (dict(rtol=-1.0), dict(rtol=float("nan")), dict(max_iter=-1)):
+        with pytest.raises(B.SptrsvError) as ei:
+            G.solve(b, **kw)
+        assert ei.value.code == 1
+    G.close()
+
+
+def test_pcg_rejects_bad_matrices():
+    from paper_2103_11445_gb300 import binding as B
+    A = mg.symmetric_from_lower(mg.stencil2d(6))
+    bad = A.col.copy()
+    bad[-1] = A.n                                          # a column outside [0, n)
+    with pytest.raises(B.SptrsvError) as ei:
+        B.PCG(A.n, A.row_ptr, bad, A.val)
+    assert ei.value.code == 2
+    # drop row 7's diagonal: D + L misses it
+    rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    keep = ~((rows == 7) & (A.col == 7))
+    cnt = np.bincount(rows[keep], minlength=A.n)
+    rp = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int32)
+    with pytest.raises(B.SptrsvError) as ei:
+        B.PCG(A.n, rp, A.col[keep], A.val[keep])
+    assert ei.value.code == 5
+    with pytest.raises(B.SptrsvError) as ei:
+        B.PCG(0, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    assert ei.value.code == 1
