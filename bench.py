@@ -858,6 +858,23 @@ def run_pcg(args, world, rank):
         if k >= 3:
             plain.append(e0.elapsed_time(e1))
     G0.close()
+    # the same iteration with the IC(0) preconditioner (fewer, equally priced steps)
+    t0 = time.perf_counter()
+    G1 = Bd.PCG(n, rp, col, val, lower=sel, upper=sel, precond=Bd.PRECOND_IC0)
+    torch.cuda.synchronize()
+    ic0_setup_ms = (time.perf_counter() - t0) * 1e3
+    ic0 = []
+    for k in range(3 + max(2, args.steps // 4)):
+        x1 = torch.zeros_like(b)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, it1, rel1 = G1.solve(b, x1, rtol=PCG_RTOL, max_iter=2000)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= 3:
+            ic0.append(e0.elapsed_time(e1))
+    ic0_true = float(np.linalg.norm(b_np - As @ x1.cpu().numpy()) / np.linalg.norm(b_np))
+    G1.close()
     # end to end: b from pinned host memory in, x out, every step
     hb = torch.from_numpy(b_np.copy()).pin_memory()
     hx = torch.empty_like(hb).pin_memory()
@@ -899,6 +916,9 @@ def run_pcg(args, world, rank):
                        "nlev": ilo["nlev"], "nlev_new": [ilo["nlev_new"], iup["nlev_new"]],
                        "plain_plans_ms_per_solve": round(statistics.mean(plain), 3),
                        "plain_plans_iterations": it0,
+                       "ic0": {"ms_per_solve": round(statistics.mean(ic0), 3),
+                               "iterations": it1, "true_relres": ic0_true,
+                               "setup_ms": round(ic0_setup_ms, 1)},
                        "trsv_kernel_ms": [round(statistics.mean(kern_lo), 4),
                                           round(statistics.mean(kern_up), 4)],
                        "trsv_share_of_step": round(it * (statistics.mean(kern_lo) +

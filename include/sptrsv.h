@@ -334,29 +334,47 @@ SPTRSV_API sptrsv_status_t sptrsv_batch_get_info(sptrsv_batch_t batch, int32_t *
                                                  int32_t *h_graph);
 SPTRSV_API void sptrsv_batch_destroy(sptrsv_batch_t batch);
 
-/* Preconditioned conjugate gradients with the symmetric Gauss-Seidel
- * preconditioner -- a consumer of the triangular solve (Sec. I names the
- * iterative solvers that spend their time in SpTRSV as the method's users).
- * For an SPD matrix A = L + D + L^T the preconditioner is
- * M = (D + L) D^{-1} (D + L)^T, applied each step as two triangular solves:
- * (D + L) y = r and (D + L)^T z = D y.
+/* Preconditioners of sptrsv_pcg_create, both built on A's lower triangle. */
+typedef enum {
+    SPTRSV_PRECOND_SGS = 0,  /* symmetric Gauss-Seidel: M = (D + L) D^{-1} (D + L)^T */
+    SPTRSV_PRECOND_IC0 = 1   /* zero-fill incomplete Cholesky: M = C C^T */
+} sptrsv_precond_t;
+
+/* Preconditioned conjugate gradients -- a consumer of the triangular solve
+ * (Sec. I names the iterative solvers that spend their time in SpTRSV as
+ * the method's users).  For an SPD matrix A = L + D + L^T the preconditioner
+ * is built on a lower triangle T with the pattern of D + L:
+ *   SPTRSV_PRECOND_SGS  T = D + L,  M = T D^{-1} T^T;
+ *   SPTRSV_PRECOND_IC0  T = C, the IC(0) factor (C C^T = A on the pattern of
+ *                       D + L, row by row: C_ij = (A_ij - sum_k C_ik C_jk) /
+ *                       C_jj over the k < j stored in both rows, C_ii =
+ *                       sqrt(A_ii - sum_k C_ik^2)),  M = C C^T.
+ * Each step applies M^{-1} as two triangular solves: T y = r, then
+ * T^T z = D y (SGS) or T^T z = y (IC(0)).
  *
  * sptrsv_pcg_create: A is the FULL symmetric matrix in device CSR
  * (row_ptr[n+1], col[nnz], val[nnz], int32 / FP64, columns ascending per
  * row, diagonal stored, n >= 1, nnz >= 1); the library copies it, so the
  * caller's arrays may be freed afterwards.  The call extracts D + L on the
- * device and builds two plans of it, one analysed as SPTRSV_OP_LOWER and one
- * as SPTRSV_OP_LOWER_TRANS, transformed with prm_lower and prm_upper (NULL:
+ * device, for IC(0) factors it (one launch per level of D + L's dependency
+ * DAG), and builds two plans of T, one analysed as SPTRSV_OP_LOWER and one as
+ * SPTRSV_OP_LOWER_TRANS, transformed with prm_lower and prm_upper (NULL:
  * sptrsv_default_params).  The PCG object owns both plans; synchronises
  * `stream`.  The library does not check that A is symmetric or positive
  * definite; the iteration has no meaning otherwise.
- * Errors: SPTRSV_ERR_INVALID_ARG (null pointer, sizes), SPTRSV_ERR_UNSORTED
- * (row_ptr not monotone inside [0, nnz]), SPTRSV_ERR_NOT_LOWER (a column
- * outside [0, n)), the analysis codes of D + L (unsorted columns, missing or
- * zero diagonal) and the transforms', SPTRSV_ERR_OOM, SPTRSV_ERR_CUDA.
+ * Errors: SPTRSV_ERR_INVALID_ARG (null pointer, sizes, unknown precond),
+ * SPTRSV_ERR_UNSORTED (row_ptr not monotone inside [0, nnz]),
+ * SPTRSV_ERR_NOT_LOWER (a column outside [0, n)), the analysis codes of
+ * D + L (unsorted columns, missing or zero diagonal), SPTRSV_ERR_ZERO_DIAG
+ * also for an IC(0) pivot <= 0 (the incomplete factorisation breaks down),
+ * the transforms' codes, SPTRSV_ERR_OOM, SPTRSV_ERR_CUDA.
  *
  * sptrsv_pcg_get_plans: the two plans (borrowed: valid until
  * sptrsv_pcg_destroy) for sptrsv_get_info, profiling or a new transform.
+ *
+ * sptrsv_pcg_get_factor: *h_nnz = entries of T; if d_val is not NULL, copies
+ * T's values (device, FP64, h_nnz) in the order of A's lower-triangle
+ * entries (row by row, columns ascending) on `stream`, asynchronously.
  *
  * sptrsv_pcg_solve: x (device, FP64, n) holds the initial guess on entry and
  * the iterate on return; b (device, FP64, n) is not modified.  Steps until
@@ -374,11 +392,14 @@ SPTRSV_API void sptrsv_batch_destroy(sptrsv_batch_t batch);
  * NaN), SPTRSV_ERR_CUDA, and the solves'. */
 SPTRSV_API sptrsv_status_t sptrsv_pcg_create(int32_t n, int64_t nnz, const int32_t *d_row_ptr,
                                              const int32_t *d_col, const double *d_val,
+                                             int32_t precond,
                                              const sptrsv_transform_params_t *prm_lower,
                                              const sptrsv_transform_params_t *prm_upper,
                                              sptrsv_stream_t stream, sptrsv_pcg_t *out);
 SPTRSV_API sptrsv_status_t sptrsv_pcg_get_plans(sptrsv_pcg_t pcg, sptrsv_plan_t *lower,
                                                 sptrsv_plan_t *upper);
+SPTRSV_API sptrsv_status_t sptrsv_pcg_get_factor(sptrsv_pcg_t pcg, int64_t *h_nnz,
+                                                 double *d_val, sptrsv_stream_t stream);
 SPTRSV_API sptrsv_status_t sptrsv_pcg_solve(sptrsv_pcg_t pcg, const double *d_b, double *d_x,
                                             double rtol, int32_t max_iter, int32_t *h_iters,
                                             double *h_relres, sptrsv_stream_t stream);

@@ -28,6 +28,7 @@ SELECT_NONE, SELECT_HEURISTIC, SELECT_COSTMODEL, SELECT_FIXED = 0, 1, 2, 3
 SOLVE_AUTO, SOLVE_BARRIER, SOLVE_SYNCFREE = 0, 1, 2
 F64, F32_IR = 0, 1
 OP_LOWER, OP_UPPER, OP_LOWER_TRANS, OP_UPPER_TRANS = 0, 1, 2, 3
+PRECOND_SGS, PRECOND_IC0 = 0, 1
 
 
 class SptrsvError(RuntimeError):
@@ -111,8 +112,9 @@ _SIGS = {
     "sptrsv_set_profiling": (c_int32, [c_void_p, c_int32]),
     "sptrsv_solve_ir_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "sptrsv_last_kernel_ms": (c_int32, [c_void_p, POINTER(ctypes.c_float)]),
-    "sptrsv_pcg_create": (c_int32, [c_int32, c_int64, c_void_p, c_void_p, c_void_p,
+    "sptrsv_pcg_create": (c_int32, [c_int32, c_int64, c_void_p, c_void_p, c_void_p, c_int32,
                                     c_void_p, c_void_p, c_void_p, POINTER(c_void_p)]),
+    "sptrsv_pcg_get_factor": (c_int32, [c_void_p, POINTER(c_int64), c_void_p, c_void_p]),
     "sptrsv_pcg_get_plans": (c_int32, [c_void_p, POINTER(c_void_p), POINTER(c_void_p)]),
     "sptrsv_pcg_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_double, c_int32,
                                    POINTER(c_int32), POINTER(c_double), c_void_p]),
@@ -351,10 +353,10 @@ def sptrsv_batch_destroy(batch: int) -> None:
 
 
 def sptrsv_pcg_create(n: int, nnz: int, d_row_ptr: int, d_col: int, d_val: int,
-                      prm_lower: TransformParams | None = None,
+                      precond: int = PRECOND_SGS, prm_lower: TransformParams | None = None,
                       prm_upper: TransformParams | None = None, stream: int = 0) -> int:
     out = c_void_p()
-    _check(load().sptrsv_pcg_create(n, nnz, d_row_ptr, d_col, d_val,
+    _check(load().sptrsv_pcg_create(n, nnz, d_row_ptr, d_col, d_val, precond,
                                     byref(prm_lower) if prm_lower is not None else None,
                                     byref(prm_upper) if prm_upper is not None else None,
                                     stream, byref(out)), "sptrsv_pcg_create")
@@ -365,6 +367,15 @@ def sptrsv_pcg_get_plans(pcg: int):
     lo, up = c_void_p(), c_void_p()
     _check(load().sptrsv_pcg_get_plans(pcg, byref(lo), byref(up)), "sptrsv_pcg_get_plans")
     return lo.value, up.value
+
+
+def sptrsv_pcg_get_factor(pcg: int, d_val: int = 0, stream: int = 0) -> int:
+    """Entries of the preconditioner's triangle; copies its values to d_val
+    when given."""
+    nnz = c_int64()
+    _check(load().sptrsv_pcg_get_factor(pcg, byref(nnz), d_val or None, stream),
+           "sptrsv_pcg_get_factor")
+    return nnz.value
 
 
 def sptrsv_pcg_solve(pcg: int, d_b: int, d_x: int, rtol: float, max_iter: int,
@@ -490,12 +501,13 @@ class Plan:
 
 
 class PCG:
-    """Owns a preconditioned-CG object (symmetric Gauss-Seidel) built from a
-    full symmetric CSR matrix in torch tensors or numpy arrays; ``lower`` and
-    ``upper`` are dicts of transform parameters for its two triangular plans
-    (None: the library defaults)."""
+    """Owns a preconditioned-CG object built from a full symmetric CSR matrix
+    in torch tensors or numpy arrays; ``precond`` is PRECOND_SGS or
+    PRECOND_IC0; ``lower`` and ``upper`` are dicts of transform parameters
+    for its two triangular plans (None: the library defaults)."""
 
-    def __init__(self, n: int, row_ptr, col, val, lower=None, upper=None, stream=None):
+    def __init__(self, n: int, row_ptr, col, val, lower=None, upper=None, stream=None,
+                 precond: int = PRECOND_SGS):
         import torch
         dev = torch.device("cuda", torch.cuda.current_device())
 
@@ -516,7 +528,7 @@ class PCG:
         rp, c, v = t(row_ptr, torch.int32), t(col, torch.int32), t(val, torch.float64)
         self._handle = 0
         self._handle = sptrsv_pcg_create(self.n, int(c.numel()), rp.data_ptr(), c.data_ptr(),
-                                         v.data_ptr(), prm(lower), prm(upper),
+                                         v.data_ptr(), int(precond), prm(lower), prm(upper),
                                          _stream_handle(stream))
 
     @property
@@ -527,6 +539,16 @@ class PCG:
         """(info of the D + L plan, info of the (D + L)^T plan)."""
         lo, up = sptrsv_pcg_get_plans(self._handle)
         return sptrsv_get_info(lo).as_dict(), sptrsv_get_info(up).as_dict()
+
+    def factor(self):
+        """The triangle's values (D + L, or the IC(0) factor) in the order of
+        A's lower-triangle entries."""
+        import torch
+        nnz = sptrsv_pcg_get_factor(self._handle)
+        out = torch.empty(nnz, dtype=torch.float64,
+                          device=torch.device("cuda", torch.cuda.current_device()))
+        sptrsv_pcg_get_factor(self._handle, out.data_ptr(), _stream_handle(None))
+        return out
 
     def solve(self, b, x=None, rtol: float = 1e-8, max_iter: int = 1000, stream=None):
         """(x, iterations, relative residual); x (if given) is the initial

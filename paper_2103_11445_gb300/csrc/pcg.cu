@@ -1,17 +1,23 @@
-// Preconditioned conjugate gradients with the symmetric Gauss-Seidel
-// preconditioner M = (D + L) D^{-1} (D + L)^T of an SPD matrix A = L + D + L^T.
+// Preconditioned conjugate gradients for an SPD matrix A = L + D + L^T with
+// one of two preconditioners built on A's lower triangle:
+//   symmetric Gauss-Seidel  M = (D + L) D^{-1} (D + L)^T,
+//   IC(0)                   M = C C^T, C the zero-fill incomplete Cholesky
+//                           factor (the pattern of D + L, C C^T = A there).
 // The triangular solve is the kernel of such preconditioners (Sec. I names
 // iterative solvers as SpTRSV's consumers): every step applies M^{-1} as two
-// of this library's solves -- (D + L) y = r on a plan of A's lower triangle,
-// (D + L)^T z = D y on a plan of the same triangle as SPTRSV_OP_LOWER_TRANS --
-// each analysed, rewritten (Sec. III) and tuned once, when the PCG object is
-// created.
+// of this library's solves -- T y = r on a plan of the triangle T (D + L or
+// C), T^T z = D y (SGS) or T^T z = y (IC(0)) on a plan of the same triangle as
+// SPTRSV_OP_LOWER_TRANS -- each analysed, rewritten (Sec. III) and tuned once,
+// when the PCG object is created.  The IC(0) factor itself is computed level
+// by level over the same dependency DAG the solve uses (row i needs the rows
+// of its pattern, Sec. II's DAG_L), one launch per level.
 //
 // The vector work (A p, dot products, updates) runs in the kernels below;
 // scalars (alpha, beta, the residual norm) stay on the device, and the host
 // reads one number per step to test convergence.  Dot products reduce in a
 // fixed order (per-block partial sums, then one block).
 #include <cmath>
+#include <vector>
 
 #include "kernels.cuh"
 #include "plan.cuh"
@@ -135,6 +141,50 @@ __global__ void tril_gather_kernel(int32_t n, const int32_t *__restrict__ rp,
         }
 }
 
+// IC(0), rows of one level (their dependencies all lie in earlier levels):
+// row i, columns j < i ascending, C_ij = (A_ij - sum_k C_ik C_jk) / C_jj over
+// the k < j stored in both rows (a merge of two sorted column lists), then
+// C_ii = sqrt(A_ii - sum_k C_ik^2).  c holds A's values on entry and C's on
+// return.  A pivot <= 0 records the row in *err (atomicMin) and stores 1 so
+// that later rows stay finite.
+__global__ void ic0_level_kernel(const int32_t *__restrict__ rows, int32_t count,
+                                 const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                 double *__restrict__ c, int32_t *err) {
+    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int32_t i = rows[t];
+    const int32_t a = rp[i], e = rp[i + 1] - 1;   // e: the diagonal, last in the row
+    double sq = 0.0;
+    for (int32_t p = a; p < e; ++p) {
+        const int32_t j = col[p];
+        const int32_t jb = rp[j], je = rp[j + 1] - 1;
+        double s = c[p];
+        int32_t q = a, r = jb;
+        while (q < p && r < je) {
+            const int32_t cq = col[q], cr = col[r];
+            if (cq == cr) {
+                s = fma(-c[q], c[r], s);
+                ++q;
+                ++r;
+            } else if (cq < cr) {
+                ++q;
+            } else {
+                ++r;
+            }
+        }
+        const double v = s / c[je];
+        c[p] = v;
+        sq = fma(v, v, sq);
+    }
+    const double d = c[e] - sq;
+    if (d > 0.0) {
+        c[e] = sqrt(d);
+    } else {
+        atomicMin(err, i);
+        c[e] = 1.0;
+    }
+}
+
 // the diagonal of A (0 where a row stores none)
 __global__ void diag_kernel(int32_t n, const int32_t *__restrict__ rp,
                             const int32_t *__restrict__ col, const double *__restrict__ val,
@@ -157,9 +207,11 @@ using namespace sptrsv;
 struct sptrsv_pcg_s {
     int32_t n = 0;
     int64_t nnz = 0;
+    int32_t precond = SPTRSV_PRECOND_SGS;
+    int32_t nnz_tri = 0;                             // entries of the triangle T
     sptrsv_plan_t lower = nullptr, upper = nullptr;   // owned
     DevArr<int32_t> rp, col;
-    DevArr<double> val, diag, r, z, p, q, y, part;
+    DevArr<double> val, tri_val, diag, r, z, p, q, y, part;
     DevArr<PcgScalars> sc;
     ~sptrsv_pcg_s() {
         sptrsv_plan_destroy(lower);
@@ -186,13 +238,49 @@ sptrsv_status_t dot(sptrsv_pcg_t g, const double *u, const double *v, double *ou
     return SPTRSV_OK;
 }
 
-// z = M^{-1} r: (D + L) y = r, then (D + L)^T z = D y
-sptrsv_status_t sgs_apply(sptrsv_pcg_t g, const double *r, double *z, cudaStream_t s) {
+// z = M^{-1} r: T y = r, then T^T z = D y (SGS) or T^T z = y (IC(0))
+sptrsv_status_t precond_apply(sptrsv_pcg_t g, const double *r, double *z, cudaStream_t s) {
     sptrsv_status_t st = sptrsv_solve(g->lower, r, g->y.p, 1, s);
     if (st != SPTRSV_OK) return st;
+    if (g->precond == SPTRSV_PRECOND_IC0) return sptrsv_solve(g->upper, g->y.p, z, 1, s);
     scale_kernel<<<blocks(g->n, 256), 256, 0, s>>>(g->n, g->diag.p, g->y.p, g->q.p);
     PCK(cudaGetLastError());
     return sptrsv_solve(g->upper, g->q.p, z, 1, s);
+}
+
+// C = IC(0) of the SPD matrix whose lower triangle is (lrp, lcol, c): levels
+// from an analysis of the triangle, then one launch per level.
+sptrsv_status_t ic0_factor(int32_t n, int32_t nnz_l, const int32_t *lrp, const int32_t *lcol,
+                           double *c, sptrsv_stream_t stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    sptrsv_plan_t tmp = nullptr;
+    sptrsv_status_t st = sptrsv_analyze(n, nnz_l, lrp, lcol, c, stream, &tmp);
+    if (st != SPTRSV_OK) return st;
+    struct Guard {
+        sptrsv_plan_t p;
+        ~Guard() { sptrsv_plan_destroy(p); }
+    } guard{tmp};
+    sptrsv_info_t info;
+    if ((st = sptrsv_get_info(tmp, &info)) != SPTRSV_OK) return st;
+    DevArr<int32_t> perm, lptr, err;
+    PCK(perm.alloc(n));
+    PCK(lptr.alloc((size_t)info.nlev + 1));
+    PCK(err.alloc(1));
+    if ((st = sptrsv_get_levels(tmp, nullptr, lptr.p, perm.p, stream)) != SPTRSV_OK) return st;
+    std::vector<int32_t> h((size_t)info.nlev + 1);
+    PCK(cudaMemcpyAsync(h.data(), lptr.p, h.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PCK(cudaMemsetAsync(err.p, 0x7f, sizeof(int32_t), s));
+    PCK(cudaStreamSynchronize(s));
+    for (int32_t l = 0; l < info.nlev; ++l) {
+        const int32_t cnt = h[l + 1] - h[l];
+        ic0_level_kernel<<<blocks(cnt, 128), 128, 0, s>>>(perm.p + h[l], cnt, lrp, lcol, c,
+                                                          err.p);
+    }
+    PCK(cudaGetLastError());
+    int32_t bad = 0;
+    PCK(cudaMemcpyAsync(&bad, err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PCK(cudaStreamSynchronize(s));
+    return bad == 0x7f7f7f7f ? SPTRSV_OK : SPTRSV_ERR_ZERO_DIAG;
 }
 
 }  // namespace
@@ -200,13 +288,15 @@ sptrsv_status_t sgs_apply(sptrsv_pcg_t g, const double *r, double *z, cudaStream
 extern "C" {
 
 sptrsv_status_t sptrsv_pcg_create(int32_t n, int64_t nnz, const int32_t *d_row_ptr,
-                                  const int32_t *d_col, const double *d_val,
+                                  const int32_t *d_col, const double *d_val, int32_t precond,
                                   const sptrsv_transform_params_t *prm_lower,
                                   const sptrsv_transform_params_t *prm_upper,
                                   sptrsv_stream_t stream, sptrsv_pcg_t *out) {
     if (!out) return SPTRSV_ERR_INVALID_ARG;
     *out = nullptr;
     if (n <= 0 || nnz <= 0 || nnz > INT32_MAX || !d_row_ptr || !d_col || !d_val)
+        return SPTRSV_ERR_INVALID_ARG;
+    if (precond != SPTRSV_PRECOND_SGS && precond != SPTRSV_PRECOND_IC0)
         return SPTRSV_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     sptrsv_pcg_s *g = new sptrsv_pcg_s();
@@ -225,6 +315,7 @@ sptrsv_status_t sptrsv_pcg_create(int32_t n, int64_t nnz, const int32_t *d_row_p
     } while (0)
     g->n = n;
     g->nnz = nnz;
+    g->precond = precond;
     PCKC(g->rp.alloc((size_t)n + 1));
     PCKC(g->col.alloc(nnz));
     PCKC(g->val.alloc(nnz));
@@ -247,9 +338,9 @@ sptrsv_status_t sptrsv_pcg_create(int32_t n, int64_t nnz, const int32_t *d_row_p
     }
     diag_kernel<<<blocks(n, 256), 256, 0, s>>>(n, g->rp.p, g->col.p, g->val.p, g->diag.p);
     PCKC(cudaGetLastError());
-    {   // D + L, analysed as the forward and as the transposed operator
+    {   // the triangle T (D + L, or its IC(0) factor), analysed as the forward
+        // and as the transposed operator
         DevArr<int32_t> cnt, lrp, lcol;
-        DevArr<double> lval;
         DevArr<int64_t> tmp;
         PCKC(cnt.alloc(n));
         PCKC(lrp.alloc((size_t)n + 1));
@@ -261,14 +352,19 @@ sptrsv_status_t sptrsv_pcg_create(int32_t n, int64_t nnz, const int32_t *d_row_p
         PCKC(cudaMemcpyAsync(&nnz_l, lrp.p + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         PCKC(cudaStreamSynchronize(s));
         if (nnz_l <= 0) return fail(SPTRSV_ERR_MISSING_DIAG);
+        g->nnz_tri = nnz_l;
         PCKC(lcol.alloc(nnz_l));
-        PCKC(lval.alloc(nnz_l));
+        PCKC(g->tri_val.alloc(nnz_l));
+        double *tv = g->tri_val.p;
         tril_gather_kernel<<<blocks(n, 256), 256, 0, s>>>(n, g->rp.p, g->col.p, g->val.p, lrp.p,
-                                                          lcol.p, lval.p);
+                                                          lcol.p, tv);
         PCKC(cudaGetLastError());
-        if ((st = sptrsv_analyze_ex(n, nnz_l, lrp.p, lcol.p, lval.p, SPTRSV_OP_LOWER, stream,
+        if (precond == SPTRSV_PRECOND_IC0 &&
+            (st = ic0_factor(n, nnz_l, lrp.p, lcol.p, tv, stream)) != SPTRSV_OK)
+            return fail(st);
+        if ((st = sptrsv_analyze_ex(n, nnz_l, lrp.p, lcol.p, tv, SPTRSV_OP_LOWER, stream,
                                     &g->lower)) != SPTRSV_OK ||
-            (st = sptrsv_analyze_ex(n, nnz_l, lrp.p, lcol.p, lval.p, SPTRSV_OP_LOWER_TRANS,
+            (st = sptrsv_analyze_ex(n, nnz_l, lrp.p, lcol.p, tv, SPTRSV_OP_LOWER_TRANS,
                                     stream, &g->upper)) != SPTRSV_OK)
             return fail(st);
         PCKC(cudaStreamSynchronize(s));
@@ -287,6 +383,18 @@ sptrsv_status_t sptrsv_pcg_get_plans(sptrsv_pcg_t g, sptrsv_plan_t *lower, sptrs
     if (!g) return SPTRSV_ERR_INVALID_ARG;
     if (lower) *lower = g->lower;
     if (upper) *upper = g->upper;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_pcg_get_factor(sptrsv_pcg_t g, int64_t *h_nnz, double *d_val,
+                                      sptrsv_stream_t stream) {
+    if (!g) return SPTRSV_ERR_INVALID_ARG;
+    if (h_nnz) *h_nnz = g->nnz_tri;
+    if (d_val) {
+        cudaStream_t s = (cudaStream_t)stream;
+        PCK(cudaMemcpyAsync(d_val, g->tri_val.p, (size_t)g->nnz_tri * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s));
+    }
     return SPTRSV_OK;
 }
 
@@ -321,7 +429,7 @@ sptrsv_status_t sptrsv_pcg_solve(sptrsv_pcg_t g, const double *d_b, double *d_x,
     double rel = std::sqrt(host[0]) / bnorm;
     int32_t it = 0;
     if (rel > rtol) {
-        if ((st = sgs_apply(g, g->r.p, g->z.p, s)) != SPTRSV_OK) return st;
+        if ((st = precond_apply(g, g->r.p, g->z.p, s)) != SPTRSV_OK) return st;
         update_p_kernel<<<vb, 256, 0, s>>>(n, sc, g->z.p, g->p.p, 1);
         PCK(cudaGetLastError());
         if ((st = dot(g, g->r.p, g->z.p, &sc->rz, s)) != SPTRSV_OK) return st;
@@ -339,7 +447,7 @@ sptrsv_status_t sptrsv_pcg_solve(sptrsv_pcg_t g, const double *d_b, double *d_x,
         PCK(cudaStreamSynchronize(s));
         rel = std::sqrt(rr) / bnorm;
         if (rel <= rtol || it >= max_iter) break;
-        if ((st = sgs_apply(g, g->r.p, g->z.p, s)) != SPTRSV_OK) return st;
+        if ((st = precond_apply(g, g->r.p, g->z.p, s)) != SPTRSV_OK) return st;
         if ((st = dot(g, g->r.p, g->z.p, &sc->rz_new, s)) != SPTRSV_OK) return st;
         update_p_kernel<<<vb, 256, 0, s>>>(n, sc, g->z.p, g->p.p, 0);
         roll_rz_kernel<<<1, 1, 0, s>>>(sc);

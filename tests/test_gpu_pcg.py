@@ -1,8 +1,9 @@
-"""GPU parity of preconditioned conjugate gradients with the symmetric
-Gauss-Seidel preconditioner (sptrsv_pcg_*): every step's two triangular
-solves run through the library's plans of the lower triangle (forward, and
-transposed), compared with the oracle's PCG (oracle/pcg.py) on the same
-inputs -- same iteration counts, iterates equal up to rounding -- and at the
+"""GPU parity of preconditioned conjugate gradients (sptrsv_pcg_*) with the
+symmetric Gauss-Seidel and the IC(0) preconditioners: every step's two
+triangular solves run through the library's plans of a lower triangle
+(forward, and transposed), compared with the oracle's PCG (oracle/pcg.py) on
+the same inputs -- same iteration counts, iterates equal up to rounding --
+the device IC(0) factor against the oracle's element by element, and at the
 full 128^3 size with properties that hold at any size (true residual within
 the tolerance, repeatability up to rounding)."""
 import numpy as np
@@ -40,32 +41,102 @@ PLANS = [
 ]
 
 
+PRECONDS = [(0, "sgs"), (1, "ic0")]
+
+
+@pytest.mark.parametrize("pc,pcname", PRECONDS, ids=[p[1] for p in PRECONDS])
 @pytest.mark.parametrize("pname,lo,up", PLANS, ids=[p[0] for p in PLANS])
 @pytest.mark.parametrize("name,make", MATS, ids=[m[0] for m in MATS])
-def test_pcg_matches_oracle(name, make, pname, lo, up):
+def test_pcg_matches_oracle(name, make, pname, lo, up, pc, pcname):
     import torch
     from paper_2103_11445_gb300 import binding as B
     A = make()
     b = mg.rhs_uniform(A.n, seed=31)
     x0 = np.random.default_rng(32).uniform(-1, 1, A.n)
-    G = B.PCG(A.n, A.row_ptr, A.col, A.val, lower=lo, upper=up)
+    G = B.PCG(A.n, A.row_ptr, A.col, A.val, lower=lo, upper=up, precond=pc)
     bt = torch.as_tensor(b, device="cuda")
     # a fixed number of steps: the iterates agree up to rounding
     for steps in (1, 5):
-        xr, itr, relr = opcg.pcg(A, b, x0, rtol=0.0, max_iter=steps)
+        xr, itr, relr = opcg.pcg(A, b, x0, rtol=0.0, max_iter=steps, precond=pcname)
         x, it, rel = G.solve(bt, torch.as_tensor(x0, device="cuda"), rtol=0.0, max_iter=steps)
         assert it == itr == steps
         assert oracle.relerr(x.cpu().numpy(), xr) <= 1e-9, (steps, name, pname)
         assert abs(rel - relr) <= 1e-8 * max(relr, 1e-300) + 1e-15
     # to convergence: the same step count (one step of slack for a residual
     # that lands within rounding of the tolerance) and the same solution
-    xr, itr, relr = opcg.pcg(A, b, np.zeros(A.n), rtol=1e-12, max_iter=2000)
+    xr, itr, relr = opcg.pcg(A, b, np.zeros(A.n), rtol=1e-12, max_iter=2000, precond=pcname)
     x, it, rel = G.solve(bt, rtol=1e-12, max_iter=2000)
     assert abs(it - itr) <= 1 and rel <= 1e-12 and relr <= 1e-12
     xs = np.linalg.solve(scipy_csr(A).toarray(), b)
     assert oracle.relerr(x.cpu().numpy(), xs) <= 1e-8
     assert oracle.relerr(x.cpu().numpy(), xr) <= 1e-8
     G.close()
+
+
+@pytest.mark.parametrize("name,make", MATS + [
+    ("stencil3d_64", lambda: mg.symmetric_from_lower(mg.stencil3d(64, seed=6)))],
+    ids=[m[0] for m in MATS] + ["stencil3d_64"])
+def test_factor_matches_oracle(name, make):
+    """The triangle behind the preconditioner: D + L copied exactly for SGS,
+    the IC(0) factor within rounding of the oracle's (same summation order;
+    1e-13 relative allows a different fused rounding)."""
+    from paper_2103_11445_gb300 import binding as B
+    A = make()
+    Lo = opcg.lower_triangle(A)
+    G = B.PCG(A.n, A.row_ptr, A.col, A.val)
+    assert np.array_equal(G.factor().cpu().numpy(), Lo.val)
+    G.close()
+    G = B.PCG(A.n, A.row_ptr, A.col, A.val, precond=1)
+    c = G.factor().cpu().numpy()
+    ref = opcg.ic0(Lo).val if A.n <= 5000 else None
+    if ref is not None:
+        assert np.max(np.abs(c - ref) / np.abs(ref)) <= 1e-13
+    else:   # at 64^3 the defining property, on 2000 sampled rows
+        rows = np.random.default_rng(7).choice(A.n, 2000, replace=False)
+        Cs = sp.csr_matrix((c, Lo.col, Lo.row_ptr), shape=(A.n, A.n))
+        As = scipy_csr(A)
+        for i in rows:
+            ci = Cs.getrow(i)
+            for j, a in zip(Lo.col[Lo.row_ptr[i]:Lo.row_ptr[i + 1]],
+                            Lo.val[Lo.row_ptr[i]:Lo.row_ptr[i + 1]]):
+                v = ci.multiply(Cs.getrow(j)).sum()
+                assert abs(v - a) <= 1e-12 * max(1.0, abs(a)), (i, j)
+    G.close()
+
+
+def test_pcg_ic0_full_stencil3d_128():
+    """IC(0)-PCG on the 128^3 7-point Laplacian: the true residual meets the
+    tolerance, in fewer steps than symmetric Gauss-Seidel needs."""
+    import torch
+    from paper_2103_11445_gb300 import binding as B
+    A = mg.symmetric_from_lower(mg.stencil3d(128))
+    b = mg.rhs_uniform(A.n, seed=41)
+    bt = torch.as_tensor(b, device="cuda")
+    its = {}
+    for pc in (0, 1):
+        G = B.PCG(A.n, A.row_ptr, A.col, A.val, lower=dict(select_mode=3, depth=2),
+                  upper=dict(select_mode=3, depth=2), precond=pc)
+        x, it, rel = G.solve(bt, rtol=1e-8, max_iter=1000)
+        assert rel <= 1e-8
+        true_rel = np.linalg.norm(b - scipy_csr(A) @ x.cpu().numpy()) / np.linalg.norm(b)
+        assert true_rel <= 1.01e-8
+        its[pc] = it
+        G.close()
+    assert its[1] < its[0]
+
+
+def test_ic0_breakdown_is_reported():
+    from paper_2103_11445_gb300 import binding as B
+    # symmetric, indefinite: [[1, 2], [2, 1]]; the second pivot is 1 - 4
+    rp = np.array([0, 2, 4], np.int32)
+    col = np.array([0, 1, 0, 1], np.int32)
+    val = np.array([1.0, 2.0, 2.0, 1.0])
+    with pytest.raises(B.SptrsvError) as ei:
+        B.PCG(2, rp, col, val, precond=1)
+    assert ei.value.code == 4
+    with pytest.raises(B.SptrsvError) as ei:
+        B.PCG(2, rp, col, val, precond=2)
+    assert ei.value.code == 1
 
 
 def test_pcg_plans_are_the_lower_triangle_in_both_operators():
