@@ -38,6 +38,17 @@ def test_reference_arm_prints_one_line_from_rank_zero():
     assert d["e2e"]["h2d_bytes_per_step"] == 0
 
 
+def test_reference_arm_on_the_pcg_workload():
+    r = torchrun(["bench.py", "--impl", "reference", "--workload", "pcg", "--gpus", "2",
+                  "--steps", "2", "--warmup", "1", "--side", "10"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "iterations/s" and d["value"] > 0
+    assert d["metric"].startswith("PCG") and "pcg_stencil3d_10" in d["config"]["workload"]
+
+
 HELPER = r"""
 import os, sys, json
 sys.path.insert(0, {root!r})
