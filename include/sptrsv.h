@@ -123,6 +123,17 @@ typedef struct {
                                 per column and row, a chunk's rows in one
                                 pass) and the autotuner times solves with
                                 that many columns; any nrhs still works. */
+    int32_t tail_rows;       /* single-CTA tail: the longest run of trailing
+                                levels with at most this many rows each (at
+                                least 8 levels, <= 256 rows) is solved by one
+                                CTA after the main kernel, with the unknowns
+                                it produces kept in shared memory and the
+                                terms from before it folded into one constant
+                                per row by a grid-wide pre-pass.  Used for
+                                one right-hand side in FP64.  0 = auto
+                                (SOLVE_AUTO times 32, 64, 128 and 256 rows and
+                                keeps the tail only if faster; none
+                                otherwise), < 0 = never, > 256 = 256. */
 } sptrsv_transform_params_t;
 
 /* Everything a caller may want to report about a plan. */
@@ -151,6 +162,8 @@ typedef struct {
     int32_t tuned_from_cache; /* 1: the last SOLVE_AUTO transform reused the launch
                                  tuned earlier in this process for a plan of the
                                  same shape (sptrsv_autotune_cache_clear) */
+    int32_t tail_rows;       /* width limit of the single-CTA tail in use (0: none) */
+    int32_t tail_levels;     /* levels it solves */
 } sptrsv_info_t;
 
 SPTRSV_API const char *sptrsv_status_string(sptrsv_status_t s);

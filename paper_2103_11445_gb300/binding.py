@@ -47,6 +47,7 @@ class TransformParams(Structure):
         ("lanes_per_row", c_int32), ("block_threads", c_int32),
         ("cta_run_rows", c_int32), ("wait_timeout_ms", c_int32),
         ("grid_blocks", c_int32), ("poll_backoff_ns", c_int32), ("nrhs_hint", c_int32),
+        ("tail_rows", c_int32),
     ]
 
 
@@ -62,7 +63,7 @@ class Info(Structure):
         ("ir_iters_last", c_int32), ("num_sms", c_int32), ("poll_backoff_ns", c_int32),
         ("chosen_depth", c_int32),
         ("analyze_ms", c_double), ("transform_ms", c_double), ("op", c_int32),
-        ("tuned_from_cache", c_int32),
+        ("tuned_from_cache", c_int32), ("tail_rows", c_int32), ("tail_levels", c_int32),
     ]
 
     def as_dict(self) -> dict:

@@ -12,6 +12,7 @@
 #include <utility>
 
 #include "plan.cuh"
+#include "tail.cuh"
 
 using namespace sptrsv;
 
@@ -444,6 +445,7 @@ sptrsv_status_t build_struct(sptrsv_plan_t p, SolveStruct<T> &ss, int L, cudaStr
     ss.L = L;
     ss.nslots = total;
     ss.built = true;
+    if ((const void *)&ss == (const void *)&p->s64) p->tail = TailStruct{};   // records of the old one
     return SPTRSV_OK;
 }
 
@@ -572,6 +574,105 @@ sptrsv_status_t count_terms(sptrsv_plan_t p, cudaStream_t s) {
     return SPTRSV_OK;
 }
 
+// Records of the single-CTA tail for width limit `rows`: the longest suffix
+// of new levels with at most `rows` rows each (none when shorter than
+// kMinTailLevels levels, or when a row has more than 16 in-tail terms).
+constexpr int32_t kMinTailLevels = 8;
+constexpr int32_t kTailWindow = 16384;   // shared-memory window of unknowns (128 KiB)
+
+sptrsv_status_t build_tail(sptrsv_plan_t p, int rows, cudaStream_t s) {
+    TailStruct &t = p->tail;
+    t = TailStruct{};
+    t.for_rows = rows;
+    t.built = true;
+    const SolveStruct<double> &ss = p->s64;
+    const int32_t nseg = (int32_t)p->seg_first.size();
+    auto lo = [&](int32_t g) { return p->h_level_ptr[p->seg_first[g]]; };
+    auto hi = [&](int32_t g) {
+        return p->h_level_ptr[p->seg_first[g] + p->seg_depth[g] + 1];
+    };
+    int32_t g0 = nseg, maxw = 0;
+    while (g0 > 0 && hi(g0 - 1) - lo(g0 - 1) <= rows) {
+        --g0;
+        maxw = std::max(maxw, hi(g0) - lo(g0));
+    }
+    if (nseg - g0 < kMinTailLevels || !ss.built || ss.run_encoded > 0) return SPTRSV_OK;
+    const int32_t P0 = lo(g0), nr = p->n - P0, nl = nseg - g0;
+    const int32_t T = std::max(32, (maxw + 31) / 32 * 32);
+    int32_t c0 = 0;
+    CK(cudaMemcpy(&c0, ss.lvl_chunk.p + g0, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    std::vector<int32_t> tlp(nl + 1);
+    for (int32_t g = 0; g < nl; ++g) tlp[g] = lo(g0 + g) - P0;
+    tlp[nl] = nr;
+    DevArr<int32_t> pos_of, cnt_a, cnt_n, flags;
+    DevArr<int64_t> tmp;
+    CK(upload(t.lp, tlp, s));
+    CK(pos_of.alloc(p->n));
+    CK(cnt_a.alloc(nr));
+    CK(cnt_n.alloc(nr));
+    CK(flags.alloc(2));
+    CK(t.aptr.alloc((size_t)nr + 1));
+    CK(tmp.alloc(scan_tmp_elems(nr)));
+    CK(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int32_t), s));
+    CK(launch_pos_of_row(p->n, ss.row_id.p, pos_of.p, s));
+    CK(launch_tail_count(c0, ss.nchunks, ss.L, p->n, ss.meta.p, ss.ecol.p, pos_of.p, P0,
+                         cnt_a.p, cnt_n.p, flags.p, flags.p + 1, s));
+    CK(exclusive_scan_i32_i64(cnt_a.p, t.aptr.p, nr, tmp.p, s));
+    int32_t hflags[2] = {0, 0};
+    int64_t na = 0;
+    CK(cudaMemcpyAsync(hflags, flags.p, sizeof(hflags), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&na, t.aptr.p + nr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hflags[1] != 0 || hflags[0] > 16) {   // no tail for this plan
+        t = TailStruct{};
+        t.for_rows = rows;
+        t.built = true;
+        return SPTRSV_OK;
+    }
+    const int32_t K = hflags[0] <= 4 ? 4 : hflags[0] <= 8 ? 8 : 16;
+    CK(t.row.alloc(nr));
+    CK(t.nn.alloc(nr));
+    CK(t.diag.alloc(nr));
+    CK(t.tcol.alloc((size_t)K * nr));
+    CK(t.tval.alloc((size_t)K * nr));
+    CK(t.acol.alloc(na > 0 ? na : 1));
+    CK(t.aval.alloc(na > 0 ? na : 1));
+    CK(t.s0.alloc(nr));
+    CK(launch_tail_fill(c0, ss.nchunks, ss.L, p->n, ss.meta.p, ss.ecol.p, ss.eval.p,
+                        ss.row_id.p, ss.diag.p, ss.chunk_level.p, g0, t.lp.p, pos_of.p, P0,
+                        kTailWindow, T, K, nr, t.aptr.p, t.row.p, t.diag.p, t.nn.p, t.tcol.p,
+                        t.tval.p, t.acol.p, t.aval.p, s));
+    CK(cudaStreamSynchronize(s));
+    t.lev0 = g0;
+    t.c0 = c0;
+    t.P0 = P0;
+    t.nrows = nr;
+    t.nlev = nl;
+    t.K = K;
+    t.T = T;
+    t.W = kTailWindow;
+    return SPTRSV_OK;
+}
+
+TailData tail_view(const TailStruct &t) {
+    TailData d;
+    d.nrows = t.nrows;
+    d.nlev = t.nlev;
+    d.K = t.K;
+    d.W = t.W;
+    d.lp = t.lp.p;
+    d.row = t.row.p;
+    d.nn = t.nn.p;
+    d.tcol = t.tcol.p;
+    d.diag = t.diag.p;
+    d.tval = t.tval.p;
+    d.aptr = t.aptr.p;
+    d.acol = t.acol.p;
+    d.aval = t.aval.p;
+    d.s0 = t.s0.p;
+    return d;
+}
+
 sptrsv_status_t apply_config(sptrsv_plan_t p, cudaStream_t s) {
     const bool f32 = p->prm.precision == SPTRSV_F32_IR;
     // run slots are encoded into the entries: a new run threshold needs a
@@ -587,7 +688,19 @@ sptrsv_status_t apply_config(sptrsv_plan_t p, cudaStream_t s) {
             CKS(build_struct<float>(p, p->s32, p->cfg.L, s));
         if (p->s32.run_encoded != runs) CKS(build_phases<float>(p, p->s32, runs, s));
     }
+    if (!f32 && runs <= 0 && p->cfg.tail_rows > 0 &&
+        (!p->tail.built || p->tail.for_rows != p->cfg.tail_rows))
+        CKS(build_tail(p, p->cfg.tail_rows, s));
     return SPTRSV_OK;
+}
+
+// The tail kernel takes over the trailing levels: one right-hand side, FP64,
+// no CTA-local runs in the main kernel.
+bool tail_active(sptrsv_plan_t p, int32_t nrhs) {
+    const int runs = p->cfg.syncfree ? 0 : p->cfg.cta_run_rows;
+    return nrhs == 1 && p->prm.precision != SPTRSV_F32_IR && runs <= 0 &&
+           p->cfg.tail_rows > 0 && p->tail.built && p->tail.for_rows == p->cfg.tail_rows &&
+           p->tail.nlev > 0;
 }
 
 sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t nrhs,
@@ -605,14 +718,14 @@ sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t 
 // search.  A plan with the same key takes the cached launch without timing.
 struct TuneKey {
     int device;
-    int32_t n, precision, nrhs_hint, lanes, block, grid, runs, backoff;
+    int32_t n, precision, nrhs_hint, lanes, block, grid, runs, backoff, tail;
     int64_t nnz, nnz_x, nnz_b;
     uint64_t shape;
     bool operator<(const TuneKey &o) const {
-        return std::tie(device, n, precision, nrhs_hint, lanes, block, grid, runs, backoff, nnz,
-                        nnz_x, nnz_b, shape) <
+        return std::tie(device, n, precision, nrhs_hint, lanes, block, grid, runs, backoff, tail,
+                        nnz, nnz_x, nnz_b, shape) <
                std::tie(o.device, o.n, o.precision, o.nrhs_hint, o.lanes, o.block, o.grid,
-                        o.runs, o.backoff, o.nnz, o.nnz_x, o.nnz_b, o.shape);
+                        o.runs, o.backoff, o.tail, o.nnz, o.nnz_x, o.nnz_b, o.shape);
     }
 };
 std::mutex g_tune_mu;
@@ -631,8 +744,8 @@ TuneKey tune_key(sptrsv_plan_t p) {
         mix(((uint64_t)(uint32_t)p->seg_first[i] << 32) | (uint32_t)p->seg_depth[i]);
     const auto &q = p->prm;
     return TuneKey{p->device, p->n, q.precision, q.nrhs_hint, q.lanes_per_row, q.block_threads,
-                   q.grid_blocks, q.cta_run_rows, q.poll_backoff_ns, p->nnz, p->nnz_x,
-                   p->nnz_b, h};
+                   q.grid_blocks, q.cta_run_rows, q.poll_backoff_ns, q.tail_rows, p->nnz,
+                   p->nnz_x, p->nnz_b, h};
 }
 
 sptrsv_status_t autotune_search(sptrsv_plan_t p, cudaStream_t s);
@@ -711,7 +824,7 @@ sptrsv_status_t autotune_search(sptrsv_plan_t p, cudaStream_t s) {
     auto same = [](const SolveConfig &a, const SolveConfig &c) {
         return a.L == c.L && a.syncfree == c.syncfree && a.block_threads == c.block_threads &&
                a.grid == c.grid && a.cta_run_rows == c.cta_run_rows &&
-               a.backoff_ns == c.backoff_ns;
+               a.backoff_ns == c.backoff_ns && a.tail_rows == c.tail_rows;
     };
     SolveConfig best = p->cfg;
     auto trial = [&](const SolveConfig &c, double *ms) -> sptrsv_status_t {
@@ -794,6 +907,19 @@ sptrsv_status_t autotune_search(sptrsv_plan_t p, cudaStream_t s) {
             CKS(trial(c, &ms));
         }
     }
+    // stage 4: the single-CTA tail over trailing levels of at most 32..256 rows
+    if (!f32 && nrt == 1 && p->prm.tail_rows >= 0 &&
+        (best.syncfree || best.cta_run_rows <= 0)) {
+        const SolveConfig b0 = best;
+        std::vector<int> widths = {32, 64, 128, 256};
+        if (p->prm.tail_rows > 0) widths = {p->prm.tail_rows};
+        for (int w : widths) {
+            SolveConfig c = b0;
+            c.tail_rows = w;
+            double ms;
+            CKS(trial(c, &ms));
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     p->cfg = best;
@@ -816,6 +942,7 @@ void resolve_params(sptrsv_plan_t p, const sptrsv_transform_params_t *in) {
     if (q.wait_timeout_ms <= 0) q.wait_timeout_ms = 5000;
     if (q.nrhs_hint < 1) q.nrhs_hint = 1;
     if (q.nrhs_hint > 32) q.nrhs_hint = 32;
+    if (q.tail_rows > 256) q.tail_rows = 256;
     p->prm = q;
     p->thin_rows_used = q.thin_rows;
 }
@@ -834,6 +961,24 @@ sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t 
         SolveData<double> sd = p->s64.view();
         sd.backoff_ns = p->cfg.backoff_ns;
         if (p->profiling) CK(cudaEventRecord(p->prof_ev[0], s));
+        if (tail_active(p, nrhs)) {
+            const TailStruct &t = p->tail;
+            if (t.c0 > 0) {
+                SolveData<double> sm = sd;
+                sm.nchunks = t.c0;     // the synchronisation-free kernel's chunks
+                sm.nphases = t.lev0;   // the barrier kernel's phases: one per level
+                LaunchCfg lc{p->cfg.block_threads, grid_for(p, 1, false)};
+                if (lc.grid <= 0) return SPTRSV_ERR_CUDA;
+                CK(launch_solve<double>(sm, b, x, n, 1, 1, p->cfg.syncfree, lc, p->status.p, tmo,
+                                        false, s));
+            }
+            CK(launch_tail(tail_view(t), b, x, t.T, s));
+            if (p->profiling) {
+                CK(cudaEventRecord(p->prof_ev[1], s));
+                p->prof_valid = true;
+            }
+            return SPTRSV_OK;
+        }
         for (int32_t c0 = 0; c0 < nrhs; c0 += 32) {
             const int nr = std::min<int32_t>(32, nrhs - c0);
             LaunchCfg lc{p->cfg.block_threads, grid_for(p, nr, false)};
@@ -1140,6 +1285,8 @@ sptrsv_status_t sptrsv_transform(sptrsv_plan_t p, const sptrsv_transform_params_
                      : p->prm.cta_run_rows > 0 ? p->prm.cta_run_rows
                                                : c.block_threads / c.L;
     if (c.syncfree) c.cta_run_rows = 0;
+    c.tail_rows = p->prm.tail_rows > 0 && (c.syncfree || c.cta_run_rows <= 0) ? p->prm.tail_rows
+                                                                             : 0;
     p->cfg = c;
     CKS(apply_config(p, s));
     if (p->prm.solve_mode == SPTRSV_SOLVE_AUTO) CKS(autotune(p, s));
@@ -1201,6 +1348,8 @@ sptrsv_status_t sptrsv_get_info(sptrsv_plan_t p, sptrsv_info_t *o) {
     o->transform_ms = p->transform_ms;
     o->op = p->op;
     o->tuned_from_cache = p->tuned_from_cache ? 1 : 0;
+    o->tail_rows = tail_active(p, 1) ? p->cfg.tail_rows : 0;
+    o->tail_levels = tail_active(p, 1) ? p->tail.nlev : 0;
     if (p->status.p) {
         DevStatus h;
         if (cudaMemcpy(&h, p->status.p, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess)

@@ -81,11 +81,27 @@ struct SolveStruct {
     }
 };
 
+// Records of the single-CTA tail (see TailData in solve.cuh).
+struct TailStruct {
+    int32_t for_rows = 0;    // width limit the records were built for
+    int32_t lev0 = 0;        // first new level of the tail
+    int32_t c0 = 0;          // its first chunk
+    int32_t P0 = 0;          // its first solve position
+    int32_t nrows = 0, nlev = 0, K = 0, T = 0, W = 0;   // nlev == 0: no tail
+    DevArr<int32_t> lp, row, nn, tcol, acol;
+    DevArr<double2> diag;
+    DevArr<double> tval, aval, s0;
+    DevArr<int64_t> aptr;
+    bool built = false;
+};
+
 struct SolveConfig {
     bool syncfree = false;
     int L = 1;
     int block_threads = 512;
     int grid = 0;
+    int tail_rows = 0;      // single-CTA tail over trailing levels of at most this
+                            // many rows (0: none)
     int cta_run_rows = 0;   // resolved threshold (<= 0: no runs)
     int backoff_ns = 0;     // synchronisation-free polling back-off
 };
@@ -117,6 +133,7 @@ struct sptrsv_plan_s {
     int64_t nnz_x = 0, nnz_b = 0;
     int32_t rows_rewritten = 0;
     sptrsv::SolveStruct<double> s64;
+    sptrsv::TailStruct tail;              // of s64 (FP64, one right-hand side)
     sptrsv::SolveStruct<float> s32;
     sptrsv_transform_params_t prm{};
     sptrsv::SolveConfig cfg;

@@ -469,6 +469,94 @@ int warps_for_cap(int cap, bool numeric, size_t *smem) {
     return w;
 }
 
+
+// ---- single-CTA tail: records built from the solve structure --------------
+
+// One thread per tail chunk: per row, the terms folded into the constant
+// (b terms, unknowns before the tail) and the in-tail terms; the largest
+// in-tail count goes to *kmax.  A run-slot entry (never present in a
+// structure built for the tail) sets *bad.
+__global__ void tail_count_kernel(int32_t c0, int32_t nchunks, int L, int32_t n,
+                                  const int4 *__restrict__ meta, const int32_t *__restrict__ ecol,
+                                  const int32_t *__restrict__ pos_of, int32_t P0,
+                                  int32_t *__restrict__ cnt_a, int32_t *__restrict__ cnt_n,
+                                  int32_t *kmax, int32_t *bad) {
+    const int32_t c = c0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (c >= nchunks) return;
+    const int4 mt = meta[c];
+    const int64_t stride = (int64_t)mt.y * L;
+    for (int32_t k = 0; k < mt.y; ++k) {
+        int32_t na = 0, nn = 0;
+        for (int32_t t = 0; t < mt.z; ++t)
+            for (int sl = 0; sl < L; ++sl) {
+                const int32_t col = ecol[mt.w + t * stride + (int64_t)k * L + sl];
+                if (col == PAD_COL) continue;
+                if (col >= 0) {
+                    if (pos_of[col] >= P0) ++nn;
+                    else ++na;
+                } else if (col >= -n) {
+                    ++na;
+                } else {
+                    *bad = 1;
+                }
+            }
+        cnt_a[mt.x + k - P0] = na;
+        cnt_n[mt.x + k - P0] = nn;
+        atomicMax(kmax, nn);
+    }
+}
+
+// The records: a term of row p reading tail position q is near when
+// (start of p's level) - q <= W - T (its window slot is not overwritten
+// before p's level), far (read from x) otherwise.
+__global__ void tail_fill_kernel(int32_t c0, int32_t nchunks, int L, int32_t n,
+                                 const int4 *__restrict__ meta, const int32_t *__restrict__ ecol,
+                                 const double *__restrict__ eval,
+                                 const int32_t *__restrict__ row_id,
+                                 const double *__restrict__ diag,
+                                 const int32_t *__restrict__ chunk_level, int32_t lev0,
+                                 const int32_t *__restrict__ tlp, const int32_t *__restrict__ pos_of,
+                                 int32_t P0, int32_t W, int32_t T, int32_t K, int32_t nr,
+                                 const int64_t *__restrict__ aptr, int32_t *__restrict__ trow,
+                                 double2 *__restrict__ tdiag, int32_t *__restrict__ tnn,
+                                 int32_t *__restrict__ tcol, double *__restrict__ tval,
+                                 int32_t *__restrict__ acol, double *__restrict__ aval) {
+    const int32_t c = c0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (c >= nchunks) return;
+    const int4 mt = meta[c];
+    const int64_t stride = (int64_t)mt.y * L;
+    const int32_t lstart = tlp[chunk_level[c] - lev0];
+    for (int32_t k = 0; k < mt.y; ++k) {
+        const int32_t p = mt.x + k - P0;
+        trow[p] = row_id[mt.x + k];
+        tdiag[p] = make_double2(diag[2 * (int64_t)(mt.x + k)], diag[2 * (int64_t)(mt.x + k) + 1]);
+        int64_t ai = aptr[p];
+        int32_t ni = 0;
+        for (int32_t t = 0; t < mt.z; ++t)
+            for (int sl = 0; sl < L; ++sl) {
+                const int64_t e = mt.w + t * stride + (int64_t)k * L + sl;
+                const int32_t col = ecol[e];
+                if (col == PAD_COL || col < -n) continue;
+                const int32_t q = col >= 0 ? pos_of[col] - P0 : -1;
+                if (q >= 0) {
+                    const int32_t slot = (lstart - q <= W - T) ? (q & (W - 1)) : ~col;
+                    tcol[(int64_t)ni * nr + p] = slot;
+                    tval[(int64_t)ni * nr + p] = eval[e];
+                    ++ni;
+                } else {
+                    acol[ai] = col;
+                    aval[ai] = eval[e];
+                    ++ai;
+                }
+            }
+        tnn[p] = ni;
+        for (int32_t j = ni; j < K; ++j) {
+            tcol[(int64_t)j * nr + p] = 0;
+            tval[(int64_t)j * nr + p] = 0.0;
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_expand_queries(int32_t nq, const int32_t *q_level, const int32_t *q_tgt,
@@ -624,6 +712,39 @@ cudaError_t launch_encode_runs(int32_t n, int L, const int32_t *row_id, const in
 cudaError_t launch_f64_to_f32(const double *a, float *b, int64_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     f64_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, b, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pos_of_row(int32_t n, const int32_t *row_id, int32_t *pos, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    pos_of_row_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, row_id, pos);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tail_count(int32_t c0, int32_t nchunks, int L, int32_t n, const int4 *meta,
+                              const int32_t *ecol, const int32_t *pos_of, int32_t P0,
+                              int32_t *cnt_a, int32_t *cnt_n, int32_t *kmax, int32_t *bad,
+                              cudaStream_t s) {
+    const int32_t m = nchunks - c0;
+    if (m <= 0) return cudaSuccess;
+    tail_count_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(c0, nchunks, L, n, meta, ecol,
+                                                                  pos_of, P0, cnt_a, cnt_n,
+                                                                  kmax, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tail_fill(int32_t c0, int32_t nchunks, int L, int32_t n, const int4 *meta,
+                             const int32_t *ecol, const double *eval, const int32_t *row_id,
+                             const double *diag, const int32_t *chunk_level, int32_t lev0,
+                             const int32_t *tlp, const int32_t *pos_of, int32_t P0, int32_t W,
+                             int32_t T, int32_t K, int32_t nr, const int64_t *aptr,
+                             int32_t *trow, double2 *tdiag, int32_t *tnn, int32_t *tcol,
+                             double *tval, int32_t *acol, double *aval, cudaStream_t s) {
+    const int32_t m = nchunks - c0;
+    if (m <= 0) return cudaSuccess;
+    tail_fill_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(
+        c0, nchunks, L, n, meta, ecol, eval, row_id, diag, chunk_level, lev0, tlp, pos_of, P0, W,
+        T, K, nr, aptr, trow, tdiag, tnn, tcol, tval, acol, aval);
     return cudaGetLastError();
 }
 
