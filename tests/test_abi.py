@@ -93,3 +93,33 @@ def test_host_side_argument_errors(lib):
     assert lib.sptrsv_transform(None, None, None) == 1
     assert lib.sptrsv_check(None, None) == 1
     lib.sptrsv_plan_destroy(None)
+
+
+def test_pcg_host_side_argument_errors(lib):
+    """The preconditioned-CG entry points refuse bad arguments before any
+    device work (no GPU needed): null output, empty matrix, null arrays, an
+    unknown preconditioner, a null object."""
+    from paper_2103_11445_gb300 import binding as B
+    out = ctypes.c_void_p()
+    fake = ctypes.c_void_p(16)   # never dereferenced: the checks come first
+    assert lib.sptrsv_pcg_create(4, 4, fake, fake, fake, 0, None, None, None, None) == 1
+    assert lib.sptrsv_pcg_create(0, 4, fake, fake, fake, 0, None, None, None,
+                                 ctypes.byref(out)) == 1
+    assert out.value is None
+    assert lib.sptrsv_pcg_create(4, 0, fake, fake, fake, 0, None, None, None,
+                                 ctypes.byref(out)) == 1
+    assert lib.sptrsv_pcg_create(4, 4, None, fake, fake, 0, None, None, None,
+                                 ctypes.byref(out)) == 1
+    assert lib.sptrsv_pcg_create(4, 4, fake, fake, fake, 2, None, None, None,
+                                 ctypes.byref(out)) == 1
+    assert lib.sptrsv_pcg_create(4, 4, fake, fake, fake, -1, None, None, None,
+                                 ctypes.byref(out)) == 1
+    it, rel = ctypes.c_int32(7), ctypes.c_double(7.0)
+    assert lib.sptrsv_pcg_solve(None, fake, fake, 1e-8, 10, ctypes.byref(it),
+                                ctypes.byref(rel), None) == 1
+    lo, up = ctypes.c_void_p(), ctypes.c_void_p()
+    assert lib.sptrsv_pcg_get_plans(None, ctypes.byref(lo), ctypes.byref(up)) == 1
+    nnz = ctypes.c_int64()
+    assert lib.sptrsv_pcg_get_factor(None, ctypes.byref(nnz), None, None) == 1
+    lib.sptrsv_pcg_destroy(None)
+    assert (B.PRECOND_SGS, B.PRECOND_IC0) == (0, 1)
