@@ -402,7 +402,7 @@ typedef enum {
  * error of either plan's solves (e.g. SPTRSV_ERR_TIMEOUT) is returned at the
  * end; calls on one PCG object must not overlap.  Errors:
  * SPTRSV_ERR_INVALID_ARG (null object, b or x, max_iter < 0, rtol < 0 or
- * NaN), SPTRSV_ERR_CUDA, and the solves'. */
+ * NaN, a b whose norm is not finite), SPTRSV_ERR_CUDA, and the solves'. */
 SPTRSV_API sptrsv_status_t sptrsv_pcg_create(int32_t n, int64_t nnz, const int32_t *d_row_ptr,
                                              const int32_t *d_col, const double *d_val,
                                              int32_t precond,

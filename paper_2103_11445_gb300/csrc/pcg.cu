@@ -421,7 +421,8 @@ sptrsv_status_t sptrsv_pcg_solve(sptrsv_pcg_t g, const double *d_b, double *d_x,
     PCK(cudaMemcpyAsync(host, &sc->rr, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     PCK(cudaStreamSynchronize(s));
     const double bnorm = std::sqrt(host[1]);
-    if (!(bnorm > 0)) {   // b = 0: the solution is x = 0
+    if (!std::isfinite(bnorm)) return SPTRSV_ERR_INVALID_ARG;   // b holds a NaN or an infinity
+    if (bnorm == 0.0) {   // b = 0: the solution is x = 0
         PCK(cudaMemsetAsync(d_x, 0, (size_t)n * sizeof(double), s));
         PCK(cudaStreamSynchronize(s));
         return SPTRSV_OK;

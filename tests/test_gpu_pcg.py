@@ -194,6 +194,11 @@ def test_pcg_degenerate_inputs():
         with pytest.raises(B.SptrsvError) as ei:
             G.solve(b, **kw)
         assert ei.value.code == 1
+    bn = b.clone()
+    bn[3] = float("nan")                                   # a b that has no norm
+    with pytest.raises(B.SptrsvError) as ei:
+        G.solve(bn)
+    assert ei.value.code == 1
     G.close()
 
 
