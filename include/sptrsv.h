@@ -455,7 +455,8 @@ SPTRSV_API sptrsv_status_t sptrsv_last_kernel_ms(sptrsv_plan_t p, float *ms);
  * write can ever satisfy.  A later synchronisation-free solve must then give
  * up after wait_timeout_ms and sptrsv_check must return SPTRSV_ERR_TIMEOUT;
  * the plan is unusable afterwards.  The row must have at least one
- * off-diagonal term (SPTRSV_ERR_UNSUPPORTED otherwise). */
+ * off-diagonal term (SPTRSV_ERR_UNSUPPORTED otherwise).  A single-CTA tail
+ * (tail_rows) is dropped: every level then runs in the main kernel. */
 SPTRSV_API sptrsv_status_t sptrsv_debug_inject_wait(sptrsv_plan_t p, int32_t row);
 
 #ifdef __cplusplus

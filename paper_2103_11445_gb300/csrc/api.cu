@@ -1489,6 +1489,9 @@ sptrsv_status_t sptrsv_debug_inject_wait(sptrsv_plan_t p, int32_t row) {
         CK(cudaMemcpy(p->s64.ecol.p + slot, &row, sizeof(int32_t), cudaMemcpyHostToDevice));
         if (p->s32.built)
             CK(cudaMemcpy(p->s32.ecol.p + slot, &row, sizeof(int32_t), cudaMemcpyHostToDevice));
+        // the single-CTA tail's records were built from the old entries: drop
+        // them, so that the main kernel (which waits, boundedly) solves every level
+        p->tail = TailStruct{};
         return SPTRSV_OK;
     }
     return SPTRSV_ERR_BAD_STATE;
