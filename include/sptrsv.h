@@ -62,7 +62,9 @@ typedef enum {
     SPTRSV_ERR_CUDA = 7,          /* a CUDA runtime call failed */
     SPTRSV_ERR_TIMEOUT = 8,       /* a bounded device wait gave up */
     SPTRSV_ERR_BAD_STATE = 9,     /* call out of order or plan already failed */
-    SPTRSV_ERR_UNSUPPORTED = 10   /* size or mode the library does not handle */
+    SPTRSV_ERR_UNSUPPORTED = 10,  /* size or mode the library does not handle */
+    SPTRSV_ERR_BREAKDOWN = 11     /* an iteration met a non-finite residual or a
+                                     non-positive curvature (p, A p) */
 } sptrsv_status_t;
 
 typedef struct sptrsv_plan_s *sptrsv_plan_t;    /* opaque, owned by the library */
@@ -80,6 +82,10 @@ enum {
                                      segment; needs sptrsv_set_costmodel */
     SPTRSV_SELECT_FIXED = 3       /* merge every `depth`+1 consecutive levels */
 };
+/* Solve kernels.  BARRIER: persistent grid, one grid barrier per level (or
+ * per run of thin levels kept inside one CTA).  SYNCFREE: no barriers, each
+ * row waits for the unknowns it reads (Sec. II).  AUTO: the autotuner times
+ * both on the plan. */
 enum { SPTRSV_SOLVE_AUTO = 0, SPTRSV_SOLVE_BARRIER = 1, SPTRSV_SOLVE_SYNCFREE = 2 };
 enum { SPTRSV_F64 = 0, SPTRSV_F32_IR = 1 };
 
@@ -134,6 +140,17 @@ typedef struct {
                                 (SOLVE_AUTO times 32, 64, 128 and 256 rows and
                                 keeps the tail only if faster; none
                                 otherwise), < 0 = never, > 256 = 256. */
+    int32_t stage_z;         /* synchronisation-free solve of one right-hand
+                                side: each warp's next chunk of rows (row ids,
+                                diagonals, columns, values) is copied into
+                                shared memory by the bulk-copy engine while
+                                the warp solves the current one, for chunks
+                                whose rows need at most stage_z steps per
+                                lane; wider chunks read global memory.
+                                0 = auto (the width of 99% of the chunks,
+                                capped so that the slots of every resident
+                                warp fit an SM's shared memory), < 0 = off,
+                                > 12 = 12. */
 } sptrsv_transform_params_t;
 
 /* Everything a caller may want to report about a plan. */
@@ -164,6 +181,8 @@ typedef struct {
                                  same shape (sptrsv_autotune_cache_clear) */
     int32_t tail_rows;       /* width limit of the single-CTA tail in use (0: none) */
     int32_t tail_levels;     /* levels it solves */
+    int32_t stage_z;         /* staging width of the FP64 one-column solve in
+                                use (0: not staged) */
 } sptrsv_info_t;
 
 SPTRSV_API const char *sptrsv_status_string(sptrsv_status_t s);
@@ -402,7 +421,11 @@ typedef enum {
  * error of either plan's solves (e.g. SPTRSV_ERR_TIMEOUT) is returned at the
  * end; calls on one PCG object must not overlap.  Errors:
  * SPTRSV_ERR_INVALID_ARG (null object, b or x, max_iter < 0, rtol < 0 or
- * NaN, a b whose norm is not finite), SPTRSV_ERR_CUDA, and the solves'. */
+ * NaN, a b whose norm is not finite), SPTRSV_ERR_BREAKDOWN (the starting
+ * residual b - A x0 is not finite, e.g. a NaN in x0; or a step met (p, A p)
+ * <= 0 or not finite, e.g. an indefinite A, or a residual that is not
+ * finite; x is then left in an unspecified state and *h_iters / *h_relres
+ * describe the step that failed), SPTRSV_ERR_CUDA, and the solves'. */
 SPTRSV_API sptrsv_status_t sptrsv_pcg_create(int32_t n, int64_t nnz, const int32_t *d_row_ptr,
                                              const int32_t *d_col, const double *d_val,
                                              int32_t precond,
@@ -455,8 +478,11 @@ SPTRSV_API sptrsv_status_t sptrsv_last_kernel_ms(sptrsv_plan_t p, float *ms);
  * write can ever satisfy.  A later synchronisation-free solve must then give
  * up after wait_timeout_ms and sptrsv_check must return SPTRSV_ERR_TIMEOUT;
  * the plan is unusable afterwards.  The row must have at least one
- * off-diagonal term (SPTRSV_ERR_UNSUPPORTED otherwise).  A single-CTA tail
- * (tail_rows) is dropped: every level then runs in the main kernel. */
+ * off-diagonal term (SPTRSV_ERR_UNSUPPORTED otherwise).  The single-CTA tail
+ * (tail_rows) is dropped and stays off for the plan's life (the tail kernel
+ * does not wait), so every level runs in the main kernel.  A later
+ * sptrsv_transform rebuilds the structure from the matrix, which removes
+ * the injected dependency. */
 SPTRSV_API sptrsv_status_t sptrsv_debug_inject_wait(sptrsv_plan_t p, int32_t row);
 
 #ifdef __cplusplus

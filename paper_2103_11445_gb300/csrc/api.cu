@@ -424,11 +424,36 @@ sptrsv_status_t build_struct(sptrsv_plan_t p, SolveStruct<T> &ss, int L, cudaStr
     CK(cudaMemcpyAsync(&total, d_off.p + nchunks, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (total > INT32_MAX) return SPTRSV_ERR_UNSUPPORTED;
+    // chunk widths: the staging width that covers 99% of the chunks
+    {
+        std::vector<int32_t> wd(nchunks);
+        CK(cudaMemcpyAsync(wd.data(), d_width.p, nchunks * sizeof(int32_t),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        std::vector<int64_t> hist(kStageZMax + 2, 0);
+        for (int32_t w : wd) ++hist[std::min<int32_t>(w, kStageZMax + 1)];
+        int64_t acc = 0;
+        ss.width_p99 = kStageZMax + 1;
+        for (int z = 0; z <= kStageZMax; ++z) {
+            acc += hist[z];
+            if (acc * 100 >= (int64_t)nchunks * 99) {
+                ss.width_p99 = z;
+                break;
+            }
+        }
+    }
     CK(ss.meta.alloc(nchunks));
+    // every chunk starts on a multiple of 4 entries and the arrays are
+    // zeroed, so the staged solve copies whole 16-byte units; row_id and
+    // diag hold a few spare elements for the same reason
     CK(ss.ecol.alloc(total));
     CK(ss.eval.alloc(total));
-    CK(ss.row_id.alloc(p->n));
-    CK(ss.diag.alloc(2 * (size_t)p->n));
+    CK(cudaMemsetAsync(ss.ecol.p, 0, (size_t)total * sizeof(int32_t), s));
+    CK(cudaMemsetAsync(ss.eval.p, 0, (size_t)total * sizeof(T), s));
+    CK(ss.row_id.alloc((size_t)p->n + 4));
+    CK(ss.diag.alloc(2 * ((size_t)p->n + 4)));
+    CK(cudaMemsetAsync(ss.row_id.p + p->n, 0, 4 * sizeof(int32_t), s));
+    CK(cudaMemsetAsync(ss.diag.p + 2 * (size_t)p->n, 0, 8 * sizeof(T), s));
     CK(launch_chunk_fill<T>(nchunks, L, d_row0.p, d_nrows.p, d_width.p, d_off.p, p->perm.p,
                             p->row_ptr.p, p->col.p, p->val.p, pos_item, p->rw_off.p,
                             p->rw_col.p, p->rw_val.p, ss.meta.p, ss.ecol.p, ss.eval.p,
@@ -440,6 +465,9 @@ sptrsv_status_t build_struct(sptrsv_plan_t p, SolveStruct<T> &ss, int L, cudaStr
     ss.n = p->n;
     ss.nlev = nseg;
     ss.nchunks = nchunks;
+    ss.h_lvl_chunk = std::move(lvl_chunk);
+    ss.sched_nw = 0;
+    ss.blob_valid = false;
     ss.run_encoded = -1;
     ss.run_slots = 0;
     ss.L = L;
@@ -521,6 +549,7 @@ sptrsv_status_t build_phases(sptrsv_plan_t p, SolveStruct<T> &ss, int run_rows, 
         CK(launch_encode_runs(p->n, ss.L, ss.row_id.p, ss.meta.p, (int32_t)run_chunk.size(),
                               d_rc.p, d_rs.p, pos.p, ss.ecol.p, s));
         CK(cudaStreamSynchronize(s));
+        ss.blob_valid = false;   // the entries changed
     }
     CK(cudaStreamSynchronize(s));
     ss.run_encoded = run_rows;
@@ -539,13 +568,25 @@ int auto_lanes(sptrsv_plan_t p) {
     return 8;
 }
 
+// Staging width of the synchronisation-free one-column solve over ss (0 =
+// not staged): the requested or 99% width, capped so that the slots of the
+// 32 warps an SM can hold fit its shared memory.
+template <typename T>
+int stage_width(sptrsv_plan_t p, const SolveStruct<T> &ss) {
+    const SolveConfig &c = p->cfg;
+    if (!c.syncfree || c.stage_off || p->prm.stage_z < 0 || !ss.built) return 0;
+    int z = p->prm.stage_z > 0 ? p->prm.stage_z : ss.width_p99;
+    z = std::min(z, stage_cap_z<T>(ss.L, p->smem_per_sm, 32));
+    return std::max(z, 0);
+}
+
 int grid_for(sptrsv_plan_t p, int nr, bool f32) {
     const SolveConfig &c = p->cfg;
     const int mx =
         f32 ? max_coresident_ctas<float>(c.L, nr, c.syncfree, c.block_threads, p->num_sms,
-                                         p->s32.run_slots)
+                                         p->s32.run_slots, nr == 1 ? stage_width(p, p->s32) : 0)
             : max_coresident_ctas<double>(c.L, nr, c.syncfree, c.block_threads, p->num_sms,
-                                          p->s64.run_slots);
+                                          p->s64.run_slots, nr == 1 ? stage_width(p, p->s64) : 0);
     if (mx <= 0) return 0;
     int g = c.grid > 0 ? c.grid : mx;
     return std::min(g, mx);
@@ -673,6 +714,56 @@ TailData tail_view(const TailStruct &t) {
     return d;
 }
 
+// Level-major chunk schedule of the synchronisation-free kernels for nw
+// warps, the autotuner's alternative to dealing the chunk list round robin:
+// each level's chunks are dealt to warps 0, 1, 2, ... in turn, and a warp
+// takes its chunks level by level, so that a warp holds about one chunk per
+// level of a wide matrix instead of one every few levels.  (On the 128^3
+// stencil it measured slower than round robin, 0.51 against 0.46 ms at depth
+// 2: every warp then polls the same level at once, which loads the L2.)
+template <typename T>
+sptrsv_status_t build_sched(SolveStruct<T> &ss, int32_t nw, cudaStream_t s) {
+    if (nw <= 0 || !ss.built || ss.nchunks == 0) return SPTRSV_OK;
+    if (ss.sched_nw == nw && ss.sched.p) return SPTRSV_OK;
+    const std::vector<int32_t> &lc = ss.h_lvl_chunk;
+    std::vector<int32_t> ptr((size_t)nw + 1, 0), sched((size_t)ss.nchunks);
+    for (size_t l = 0; l + 1 < lc.size(); ++l)
+        for (int32_t i = 0; i < lc[l + 1] - lc[l]; ++i) ++ptr[(size_t)(i % nw) + 1];
+    for (int32_t w = 0; w < nw; ++w) ptr[(size_t)w + 1] += ptr[w];
+    std::vector<int32_t> pos(ptr.begin(), ptr.end() - 1);
+    for (size_t l = 0; l + 1 < lc.size(); ++l)
+        for (int32_t i = 0; i < lc[l + 1] - lc[l]; ++i) sched[pos[i % nw]++] = lc[l] + i;
+    CK(upload(ss.sched, sched, s));
+    CK(upload(ss.sched_ptr, ptr, s));
+    CK(cudaStreamSynchronize(s));
+    ss.sched_nw = nw;
+    return SPTRSV_OK;
+}
+
+// Chunk blobs of the staged kernels: every chunk once more as one
+// contiguous run of 16-byte units (BlobLayout), built from the entries.
+template <typename T>
+sptrsv_status_t build_blob(SolveStruct<T> &ss, cudaStream_t s) {
+    if (!ss.built || ss.blob_valid || ss.nchunks == 0) return SPTRSV_OK;
+    DevArr<int64_t> units, tmp;
+    CK(units.alloc(ss.nchunks));
+    CK(ss.bofs.alloc((size_t)ss.nchunks + 1));
+    CK(tmp.alloc(scan_tmp_elems(ss.nchunks)));
+    CK(launch_blob_units<T>(ss.nchunks, ss.L, ss.meta.p, units.p, s));
+    CK(exclusive_scan_i64_i64(units.p, ss.bofs.p, ss.nchunks, tmp.p, s));
+    int64_t total = 0;
+    CK(cudaMemcpyAsync(&total, ss.bofs.p + ss.nchunks, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                       s));
+    CK(cudaStreamSynchronize(s));
+    CK(ss.blob.alloc((size_t)total));
+    CK(cudaMemsetAsync(ss.blob.p, 0, (size_t)total * sizeof(uint4), s));
+    CK(launch_blob_fill<T>(ss.nchunks, ss.L, ss.meta.p, ss.row_id.p, ss.diag.p, ss.ecol.p,
+                           ss.eval.p, ss.bofs.p, ss.blob.p, s));
+    CK(cudaStreamSynchronize(s));
+    ss.blob_valid = true;
+    return SPTRSV_OK;
+}
+
 sptrsv_status_t apply_config(sptrsv_plan_t p, cudaStream_t s) {
     const bool f32 = p->prm.precision == SPTRSV_F32_IR;
     // run slots are encoded into the entries: a new run threshold needs a
@@ -688,9 +779,21 @@ sptrsv_status_t apply_config(sptrsv_plan_t p, cudaStream_t s) {
             CKS(build_struct<float>(p, p->s32, p->cfg.L, s));
         if (p->s32.run_encoded != runs) CKS(build_phases<float>(p, p->s32, runs, s));
     }
-    if (!f32 && runs <= 0 && p->cfg.tail_rows > 0 &&
+    if (!f32 && runs <= 0 && p->cfg.tail_rows > 0 && !p->injected &&
         (!p->tail.built || p->tail.for_rows != p->cfg.tail_rows))
         CKS(build_tail(p, p->cfg.tail_rows, s));
+    // schedule and chunk blobs of the synchronisation-free kernels
+    if (p->cfg.syncfree) {
+        const int32_t nw = grid_for(p, 1, f32) * (p->cfg.block_threads / 32);
+        if (p->cfg.sched_lm) {
+            if (f32) CKS(build_sched(p->s32, nw, s));
+            else CKS(build_sched(p->s64, nw, s));
+        }
+        if (f32 ? stage_width(p, p->s32) > 0 : stage_width(p, p->s64) > 0) {
+            if (f32) CKS(build_blob(p->s32, s));
+            else CKS(build_blob(p->s64, s));
+        }
+    }
     return SPTRSV_OK;
 }
 
@@ -698,7 +801,7 @@ sptrsv_status_t apply_config(sptrsv_plan_t p, cudaStream_t s) {
 // no CTA-local runs in the main kernel.
 bool tail_active(sptrsv_plan_t p, int32_t nrhs) {
     const int runs = p->cfg.syncfree ? 0 : p->cfg.cta_run_rows;
-    return nrhs == 1 && p->prm.precision != SPTRSV_F32_IR && runs <= 0 &&
+    return !p->injected && nrhs == 1 && p->prm.precision != SPTRSV_F32_IR && runs <= 0 &&
            p->cfg.tail_rows > 0 && p->tail.built && p->tail.for_rows == p->cfg.tail_rows &&
            p->tail.nlev > 0;
 }
@@ -718,14 +821,14 @@ sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t 
 // search.  A plan with the same key takes the cached launch without timing.
 struct TuneKey {
     int device;
-    int32_t n, precision, nrhs_hint, lanes, block, grid, runs, backoff, tail;
+    int32_t n, precision, nrhs_hint, lanes, block, grid, runs, backoff, tail, stage;
     int64_t nnz, nnz_x, nnz_b;
     uint64_t shape;
     bool operator<(const TuneKey &o) const {
         return std::tie(device, n, precision, nrhs_hint, lanes, block, grid, runs, backoff, tail,
-                        nnz, nnz_x, nnz_b, shape) <
+                        stage, nnz, nnz_x, nnz_b, shape) <
                std::tie(o.device, o.n, o.precision, o.nrhs_hint, o.lanes, o.block, o.grid,
-                        o.runs, o.backoff, o.tail, o.nnz, o.nnz_x, o.nnz_b, o.shape);
+                        o.runs, o.backoff, o.tail, o.stage, o.nnz, o.nnz_x, o.nnz_b, o.shape);
     }
 };
 std::mutex g_tune_mu;
@@ -744,7 +847,7 @@ TuneKey tune_key(sptrsv_plan_t p) {
         mix(((uint64_t)(uint32_t)p->seg_first[i] << 32) | (uint32_t)p->seg_depth[i]);
     const auto &q = p->prm;
     return TuneKey{p->device, p->n, q.precision, q.nrhs_hint, q.lanes_per_row, q.block_threads,
-                   q.grid_blocks, q.cta_run_rows, q.poll_backoff_ns, q.tail_rows, p->nnz,
+                   q.grid_blocks, q.cta_run_rows, q.poll_backoff_ns, q.tail_rows, q.stage_z, p->nnz,
                    p->nnz_x, p->nnz_b, h};
 }
 
@@ -824,7 +927,8 @@ sptrsv_status_t autotune_search(sptrsv_plan_t p, cudaStream_t s) {
     auto same = [](const SolveConfig &a, const SolveConfig &c) {
         return a.L == c.L && a.syncfree == c.syncfree && a.block_threads == c.block_threads &&
                a.grid == c.grid && a.cta_run_rows == c.cta_run_rows &&
-               a.backoff_ns == c.backoff_ns && a.tail_rows == c.tail_rows;
+               a.backoff_ns == c.backoff_ns && a.tail_rows == c.tail_rows &&
+               a.stage_off == c.stage_off && a.sched_lm == c.sched_lm;
     };
     SolveConfig best = p->cfg;
     auto trial = [&](const SolveConfig &c, double *ms) -> sptrsv_status_t {
@@ -835,7 +939,8 @@ sptrsv_status_t autotune_search(sptrsv_plan_t p, cudaStream_t s) {
             }
         *ms = 1e30;
         p->cfg = c;
-        if (c.grid > 0 && grid_for(p, nrt, f32) < c.grid) return SPTRSV_OK;  // not co-resident
+        const int gmax = grid_for(p, nrt, f32);
+        if (gmax <= 0 || (c.grid > 0 && gmax < c.grid)) return SPTRSV_OK;  // not co-resident
         CKS(time_cfg(ms));
         tried.push_back({c, *ms});
         if (*ms < best_ms) {
@@ -877,8 +982,8 @@ sptrsv_status_t autotune_search(sptrsv_plan_t p, cudaStream_t s) {
             c.backoff_ns = backoff0;
             c.cta_run_rows = mode == 1 ? 1 : 0;  // set from the block size by shaped()
             double pm = 1e30;
-            for (const auto &sh : {std::make_pair(128, 4), std::make_pair(128, 8),
-                                   std::make_pair(512, 1)}) {
+            const std::pair<int, int> shapes[3] = {{128, 4}, {128, 8}, {512, 1}};
+            for (const auto &sh : shapes) {
                 double ms;
                 CKS(trial(shaped(c, sh.first, sh.second), &ms));
                 pm = std::min(pm, ms);
@@ -893,6 +998,7 @@ sptrsv_status_t autotune_search(sptrsv_plan_t p, cudaStream_t s) {
         if (pairs[i].ms >= 1e30) break;
         for (int bt : {128, 256, 512})
             for (int per_sm : {1, 2, 4, 8}) {
+                if (bt * per_sm > 2048) continue;
                 double ms;
                 CKS(trial(shaped(pairs[i].c, bt, per_sm), &ms));
             }
@@ -906,6 +1012,20 @@ sptrsv_status_t autotune_search(sptrsv_plan_t p, cudaStream_t s) {
             double ms;
             CKS(trial(c, &ms));
         }
+    }
+    // stage 3b: the synchronisation-free kernel with its chunks dealt
+    // level-major instead of round robin, and without shared-memory staging
+    if (best.syncfree) {
+        SolveConfig c = best;
+        c.sched_lm = true;
+        double ms;
+        CKS(trial(c, &ms));
+    }
+    if (best.syncfree && p->prm.stage_z == 0 && nrt == 1) {
+        SolveConfig c = best;
+        c.stage_off = true;
+        double ms;
+        CKS(trial(c, &ms));
     }
     // stage 4: the single-CTA tail over trailing levels of at most 32..256 rows
     if (!f32 && nrt == 1 && p->prm.tail_rows >= 0 &&
@@ -943,6 +1063,7 @@ void resolve_params(sptrsv_plan_t p, const sptrsv_transform_params_t *in) {
     if (q.nrhs_hint < 1) q.nrhs_hint = 1;
     if (q.nrhs_hint > 32) q.nrhs_hint = 32;
     if (q.tail_rows > 256) q.tail_rows = 256;
+    if (q.stage_z > kStageZMax) q.stage_z = kStageZMax;
     p->prm = q;
     p->thin_rows_used = q.thin_rows;
 }
@@ -960,6 +1081,8 @@ sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t 
     if (p->prm.precision != SPTRSV_F32_IR) {
         SolveData<double> sd = p->s64.view();
         sd.backoff_ns = p->cfg.backoff_ns;
+        sd.stage_z = stage_width(p, p->s64);
+        if (!p->cfg.sched_lm) sd.sched = nullptr;
         if (p->profiling) CK(cudaEventRecord(p->prof_ev[0], s));
         if (tail_active(p, nrhs)) {
             const TailStruct &t = p->tail;
@@ -998,6 +1121,8 @@ sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t 
     CKS(ensure_ir(p, count));
     SolveData<float> sd = p->s32.view();
     sd.backoff_ns = p->cfg.backoff_ns;
+    sd.stage_z = stage_width(p, p->s32);
+    if (!p->cfg.sched_lm) sd.sched = nullptr;
     auto solve32 = [&](const double *rhs, bool skip) -> sptrsv_status_t {
         for (int32_t c0 = 0; c0 < nrhs; c0 += 32) {
             const int nr = std::min<int32_t>(32, nrhs - c0);
@@ -1038,6 +1163,7 @@ const char *sptrsv_status_string(sptrsv_status_t s) {
     case SPTRSV_ERR_TIMEOUT: return "a bounded device wait timed out";
     case SPTRSV_ERR_BAD_STATE: return "plan in a bad state (call order or earlier failure)";
     case SPTRSV_ERR_UNSUPPORTED: return "unsupported size or mode";
+    case SPTRSV_ERR_BREAKDOWN: return "iteration breakdown (non-finite residual or curvature <= 0)";
     }
     return "unknown status";
 }
@@ -1097,6 +1223,8 @@ sptrsv_status_t sptrsv_analyze_ex(int32_t n, int64_t nnz, const int32_t *d_row_p
     } while (0)
     CKP(cudaGetDevice(&p->device));
     CKP(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+    CKP(cudaDeviceGetAttribute(&p->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
+                               p->device));
     p->n = n;
     p->nnz = nnz;
     p->op = op;
@@ -1269,7 +1397,8 @@ sptrsv_status_t sptrsv_transform(sptrsv_plan_t p, const sptrsv_transform_params_
     SolveConfig c;
     c.syncfree = p->prm.solve_mode == SPTRSV_SOLVE_SYNCFREE;
     c.block_threads = p->prm.block_threads > 0 ? p->prm.block_threads : 512;
-    c.grid = p->prm.grid_blocks > 0 ? p->prm.grid_blocks : (c.syncfree ? 0 : p->num_sms);
+    c.grid = p->prm.grid_blocks > 0 ? p->prm.grid_blocks
+                                    : (c.syncfree ? 0 : p->num_sms);
     c.backoff_ns = p->prm.poll_backoff_ns > 0 ? p->prm.poll_backoff_ns : 0;
     c.L = 1;
     p->cfg = c;
@@ -1350,6 +1479,7 @@ sptrsv_status_t sptrsv_get_info(sptrsv_plan_t p, sptrsv_info_t *o) {
     o->tuned_from_cache = p->tuned_from_cache ? 1 : 0;
     o->tail_rows = tail_active(p, 1) ? p->cfg.tail_rows : 0;
     o->tail_levels = tail_active(p, 1) ? p->tail.nlev : 0;
+    o->stage_z = p->prm.precision == SPTRSV_F32_IR ? 0 : stage_width(p, p->s64);
     if (p->status.p) {
         DevStatus h;
         if (cudaMemcpy(&h, p->status.p, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess)
@@ -1490,8 +1620,16 @@ sptrsv_status_t sptrsv_debug_inject_wait(sptrsv_plan_t p, int32_t row) {
         if (p->s32.built)
             CK(cudaMemcpy(p->s32.ecol.p + slot, &row, sizeof(int32_t), cudaMemcpyHostToDevice));
         // the single-CTA tail's records were built from the old entries: drop
-        // them, so that the main kernel (which waits, boundedly) solves every level
+        // them and keep the tail off for good (a later transform would build
+        // it from the injected entries, and the tail kernel does not wait), so
+        // that the main kernel, whose waits are bounded, solves every level
         p->tail = TailStruct{};
+        p->injected = true;
+        // the staged kernels read the chunks' blobs: rebuild them
+        const bool had64 = p->s64.blob_valid, had32 = p->s32.blob_valid;
+        p->s64.blob_valid = p->s32.blob_valid = false;
+        if (had64) CKS(build_blob(p->s64, 0));
+        if (had32) CKS(build_blob(p->s32, 0));
         return SPTRSV_OK;
     }
     return SPTRSV_ERR_BAD_STATE;

@@ -182,6 +182,71 @@ __device__ __forceinline__ void l2_prefetch_slice(const void *p, size_t bytes) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Shared-memory mbarriers and bulk (TMA) copies global -> shared memory.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(count) : "memory");
+}
+// makes mbarrier initialisations visible to the bulk-copy (async) proxy
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// orders this thread's earlier generic-proxy accesses of shared memory before
+// later bulk copies into it
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(bar), "r"(bytes) : "memory");
+}
+// Bulk copy of `bytes` (a positive multiple of 16; both addresses 16-byte
+// aligned) from global memory into this CTA's shared memory, completing on
+// the mbarrier's transaction count.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+                 "[%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+// 16-byte asynchronous copy global -> shared memory (through L2 only) and
+// the arrival on an mbarrier once all of this thread's earlier such copies
+// have landed (the barrier's expected count includes this arrival).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_mbar_arrive(uint32_t bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" :: "r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Bounded wait for the completion of phase `parity`; false if it gave up
+// (timeout latched, or another wait of the launch aborted).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, DevStatus *st,
+                                          uint64_t timeout_ns, int where) {
+    if (mbar_try_wait(bar, parity)) return true;
+    WaitBudget wb(timeout_ns);
+    unsigned it = 0;
+    while (!mbar_try_wait(bar, parity)) {
+        if ((++it & 15) == 0 && wb.expired(st, where)) return false;
+    }
+    return true;
+}
+// Bounded wait that latches nothing (draining copies after an abort).
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, uint64_t timeout_ns) {
+    const uint64_t deadline = globaltimer_ns() + timeout_ns;
+    while (!mbar_try_wait(bar, parity))
+        if (globaltimer_ns() > deadline) return;
+}
+
 // Called once by every CTA at the very end of a kernel that used
 // grid_barrier: the last CTA to leave resets the counters for the next
 // launch on the same stream.

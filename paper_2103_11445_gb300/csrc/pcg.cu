@@ -429,6 +429,12 @@ sptrsv_status_t sptrsv_pcg_solve(sptrsv_pcg_t g, const double *d_b, double *d_x,
     }
     double rel = std::sqrt(host[0]) / bnorm;
     int32_t it = 0;
+    // a NaN or an infinity in x0 (or in A): both rel > rtol and rel <= rtol
+    // would be false, and the loop would end at once with a garbage x
+    if (!std::isfinite(rel)) {
+        if (h_relres) *h_relres = rel;
+        return SPTRSV_ERR_BREAKDOWN;
+    }
     if (rel > rtol) {
         if ((st = precond_apply(g, g->r.p, g->z.p, s)) != SPTRSV_OK) return st;
         update_p_kernel<<<vb, 256, 0, s>>>(n, sc, g->z.p, g->p.p, 1);
@@ -443,10 +449,17 @@ sptrsv_status_t sptrsv_pcg_solve(sptrsv_pcg_t g, const double *d_b, double *d_x,
         PCK(cudaGetLastError());
         ++it;
         if ((st = dot(g, g->r.p, g->r.p, &sc->rr, s)) != SPTRSV_OK) return st;
-        double rr = 0;
-        PCK(cudaMemcpyAsync(&rr, &sc->rr, sizeof(double), cudaMemcpyDeviceToHost, s));
+        double pq_rr[2] = {0, 0};   // (p, A p) and (r, r) are adjacent
+        PCK(cudaMemcpyAsync(pq_rr, &sc->pq, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
         PCK(cudaStreamSynchronize(s));
-        rel = std::sqrt(rr) / bnorm;
+        rel = std::sqrt(pq_rr[1]) / bnorm;
+        // breakdown: an indefinite A (or preconditioner) gives (p, A p) <= 0,
+        // and any non-finite value would otherwise end the loop as if converged
+        if (!(pq_rr[0] > 0.0) || !std::isfinite(pq_rr[0]) || !std::isfinite(rel)) {
+            if (h_iters) *h_iters = it;
+            if (h_relres) *h_relres = rel;
+            return SPTRSV_ERR_BREAKDOWN;
+        }
         if (rel <= rtol || it >= max_iter) break;
         if ((st = precond_apply(g, g->r.p, g->z.p, s)) != SPTRSV_OK) return st;
         if ((st = dot(g, g->r.p, g->z.p, &sc->rz_new, s)) != SPTRSV_OK) return st;

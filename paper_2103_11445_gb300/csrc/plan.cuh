@@ -60,6 +60,13 @@ struct SolveStruct {
     DevArr<int32_t> chunk_run_p0;  // first position of the chunk's run, -1 outside runs
     int32_t run_encoded = -1;   // run threshold the entries are encoded for (-1: none)
     int64_t nslots = 0;
+    int32_t width_p99 = 0;      // steps per lane covering 99% of the chunks
+    std::vector<int32_t> h_lvl_chunk;  // host copy of lvl_chunk
+    DevArr<int32_t> sched, sched_ptr;  // level-major chunk schedule (SolveData)
+    int32_t sched_nw = 0;              // warps it was dealt to (0: none)
+    DevArr<uint4> blob;                // chunk blobs of the staged kernels
+    DevArr<int64_t> bofs;              // [nchunks + 1] unit offsets into blob
+    bool blob_valid = false;           // blob matches the current entries
     bool built = false;
     SolveData<T> view() const {
         SolveData<T> v;
@@ -77,6 +84,12 @@ struct SolveStruct {
         v.nphases = nphases;
         v.backoff_ns = 0;
         v.run_slots = run_slots;
+        v.stage_z = 0;          // set per launch (stage_width)
+        v.sched = sched.p;
+        v.sched_ptr = sched_ptr.p;
+        v.sched_nw = sched.p ? sched_nw : 0;
+        v.blob = blob_valid ? blob.p : nullptr;
+        v.bofs = blob_valid ? bofs.p : nullptr;
         return v;
     }
 };
@@ -104,6 +117,8 @@ struct SolveConfig {
                             // many rows (0: none)
     int cta_run_rows = 0;   // resolved threshold (<= 0: no runs)
     int backoff_ns = 0;     // synchronisation-free polling back-off
+    bool stage_off = false; // synchronisation-free solve without shared-memory staging
+    bool sched_lm = false;  // synchronisation-free chunks dealt level-major (else round robin)
 };
 
 }  // namespace sptrsv
@@ -111,6 +126,7 @@ struct SolveConfig {
 struct sptrsv_plan_s {
     int device = 0;
     int num_sms = 0;
+    int smem_per_sm = 0;         // shared memory of one SM (bytes)
     int32_t n = 0;
     int64_t nnz = 0;
     int32_t op = 0;              // SPTRSV_OP_* the caller asked for
@@ -146,6 +162,7 @@ struct sptrsv_plan_s {
     sptrsv_mlp_t costmodel = nullptr;  // not owned
     int32_t chosen_depth = -1;         // depth picked by the cost model (-1: none)
     bool tuned_from_cache = false;     // the last autotuning reused a cached launch
+    bool injected = false;             // sptrsv_debug_inject_wait was applied: no tail
     // profiling: events around the main solve kernel of the last solve
     bool profiling = false;
     cudaEvent_t prof_ev[2] = {nullptr, nullptr};

@@ -512,6 +512,33 @@ __device__ __forceinline__ int32_t first_chunk_of_phase(const SolveData<T> &sd, 
     return c < __ldg(&sd.lvl_chunk[p.x + 1]) ? c : -1;
 }
 
+// The chunks one warp of a synchronisation-free launch solves, in order:
+// the level-major schedule when it was dealt to this many warps, else every
+// nw-th chunk.  Chunks at or past sd.nchunks (a tail solved by another
+// kernel) end the sequence: they come after all others in both orders.
+struct WarpChunks {
+    const int32_t *list;   // schedule slice of this warp, or null
+    int32_t count;
+    int32_t gw, nw, nchunks;
+    __device__ __forceinline__ int32_t at(int32_t j) const {
+        if (list) {
+            if (j >= count) return -1;
+            const int32_t c = __ldg(list + j);
+            return c < nchunks ? c : -1;
+        }
+        const int64_t c = (int64_t)gw + (int64_t)j * nw;
+        return c < nchunks ? (int32_t)c : -1;
+    }
+};
+template <typename T>
+__device__ __forceinline__ WarpChunks warp_chunks(const SolveData<T> &sd, int32_t gw, int32_t nw) {
+    if (sd.sched && sd.sched_nw == nw) {
+        const int32_t a = __ldg(sd.sched_ptr + gw), b = __ldg(sd.sched_ptr + gw + 1);
+        return WarpChunks{sd.sched + a, b - a, gw, nw, sd.nchunks};
+    }
+    return WarpChunks{nullptr, 0, gw, nw, sd.nchunks};
+}
+
 template <typename T, int L, int R>
 __global__ void __launch_bounds__(kMaxSolveThreads)
 solve_barrier_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr,
@@ -600,10 +627,327 @@ solve_syncfree_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, int nr
     // (Staging the next chunk's entries while this one waits measured slower
     // here than processing each chunk in turn: the staged loads compete with
     // the polls and pin registers; the barrier kernel keeps its staging.)
-    for (int32_t c = gw; c < sd.nchunks; c += nw)
+    const WarpChunks wc = warp_chunks(sd, gw, nw);
+    int32_t c = wc.at(0);
+    for (int32_t j = 1; c >= 0; ++j) {
+        const int32_t cn = wc.at(j);   // in flight while this chunk runs
         if (process_chunk<T, L, R, true>(sd, c, out, cx)) break;
+        c = cn;
+    }
     grid_exit(st);
 }
+
+// ---------------------------------------------------------------------------
+// Staged synchronisation-free solve, one right-hand side.
+//
+// Without staging a chunk issues, before its first gather, the load of its
+// descriptor and then of its entries from HBM (measured on the 128^3 stencil
+// at depth 2: 0.17 + 1.3 us ahead of a 0.7 us gather, per chunk).  Here each
+// warp owns three shared-memory slots in a ring: while it solves the chunk in
+// one, the next ones are copied in -- each chunk is stored once more as one
+// contiguous blob (BlobLayout), so that the warp's 32 lanes bring it in with
+// 16-byte asynchronous copies that complete on the slot's mbarrier -- and a
+// chunk starts with all its gathers of x and b in flight at once, read from
+// shared memory.  The copies of the chunk two ahead are issued right after
+// this chunk's gathers, into the slot the previous chunk freed, so they
+// overlap the gathers' latency.  (The bulk-copy engine was tried first: four
+// small bulk copies per chunk cost 0.25-0.45 us to issue under load, and one
+// engine per SM serialises 32 warps' requests.)
+constexpr int kStageSlots = 3;
+// per warp: the slots' headers (chunk, units; 16 bytes each) and mbarriers
+// (8 bytes each), padded to 16 bytes, then the slots
+constexpr int kStageHeadBytes = (kStageSlots * 24 + 15) & ~15;
+
+// Units one slot holds: a chunk of 32 / L rows and z steps per lane.
+template <typename T>
+__host__ __device__ constexpr int stage_slot_units(int L, int z) {
+    return BlobLayout<T>(32 / L, z, L).units;
+}
+template <typename T>
+__host__ __device__ constexpr int stage_warp_bytes(int L, int z) {
+    return kStageHeadBytes + kStageSlots * 16 * stage_slot_units<T>(L, z);
+}
+
+// The warp's slot ring (shared memory).
+template <typename T>
+struct StageRing {
+    unsigned char *base;   // this warp's region
+    int cap;               // units per slot
+    __device__ __forceinline__ int4 *hdr(int sl) const {
+        return reinterpret_cast<int4 *>(base) + sl;
+    }
+    __device__ __forceinline__ uint32_t bar(int sl) const {
+        return smem_u32(base) + 16 * kStageSlots + 8 * sl;
+    }
+    __device__ __forceinline__ unsigned char *slot(int sl) const {
+        return base + kStageHeadBytes + sl * 16 * cap;
+    }
+    // true if slot sl received (or is receiving) the chunk it holds
+    __device__ __forceinline__ bool staged(int sl) const {
+        const int4 h = *hdr(sl);
+        return h.x >= 0 && h.y <= cap;
+    }
+    // All 32 lanes: slot sl takes chunk c (blob units [u0, u1)); copies are
+    // started when it fits, and every lane arrives on the slot's barrier.
+    __device__ __forceinline__ void fill(const SolveData<T> &sd, int sl, int32_t c, int64_t u0,
+                                         int64_t u1) const {
+        const int lane = threadIdx.x & 31;
+        const int units = c >= 0 ? (int)(u1 - u0) : 0;
+        if (lane == 0) *hdr(sl) = make_int4(c, units, 0, 0);
+        if (c < 0 || units > cap) return;
+        const uint32_t dst = smem_u32(slot(sl));
+        const uint4 *src = sd.blob + u0;
+        for (int u = lane; u < units; u += 32) cp_async16(dst + 16u * u, src + u);
+        cp_async_mbar_arrive(bar(sl));
+    }
+};
+
+// The refill of the ring that one chunk carries out once its gathers are in
+// flight (or before an unstaged chunk): slot sl takes chunk c.
+template <typename T>
+struct Refill {
+    const SolveData<T> &sd;
+    StageRing<T> ring;
+    int sl;
+    int32_t c;
+    int64_t u0, u1;
+    __device__ __forceinline__ void operator()() const { ring.fill(sd, sl, c, u0, u1); }
+};
+
+// U steps of one lane's entries from the slot: U gathers in flight together,
+// the terms already computed first, then the late arrivals, all still
+// pending polled together (one round trip per round, not one per term).
+// `hook` runs once the gathers are issued, if still pending (the ring's refill).
+template <typename T, int U, typename Hook>
+__device__ __forceinline__ void staged_steps(const int32_t *scol, const T *sval, int stride,
+                                             T *out, const Ctx &cx, T &acc, bool &bail,
+                                             const Hook &hook, bool &hook_pending) {
+    int32_t cc[U];
+    typename Bits<T>::U xb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) cc[u] = scol[u * stride];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (cc[u] >= 0) xb[u] = Bits<T>::poll(out + (int64_t)cc[u] * cx.ld);
+        else xb[u] = Bits<T>::of(other_term<T>(cx, cc[u], out, 0));
+    }
+    if (hook_pending) {
+        hook();
+        hook_pending = false;
+    }
+    unsigned pend = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (cc[u] >= 0 && xb[u] == Sentinel<T>::bits) pend |= 1u << u;
+        else acc = fma(-sval[u * stride], Bits<T>::from(xb[u]), acc);
+    }
+    if (pend == 0) return;
+    WaitBudget wb(cx.timeout_ns);
+    unsigned it = 0;
+    do {
+        if (cx.backoff_ns) __nanosleep(cx.backoff_ns);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (pend & (1u << u)) xb[u] = Bits<T>::poll(out + (int64_t)cc[u] * cx.ld);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if ((pend & (1u << u)) && xb[u] != Sentinel<T>::bits) {
+                acc = fma(-sval[u * stride], Bits<T>::from(xb[u]), acc);
+                pend &= ~(1u << u);
+            }
+        if (pend && (++it & kPollMask) == 0 && wb.expired(cx.st, -2)) {
+            bail = true;
+            return;
+        }
+    } while (pend);
+}
+
+template <typename T, int L>
+__device__ __forceinline__ bool chunk_staged(const unsigned char *slot, T *out, const Ctx &cx,
+                                             const Refill<T> &refill) {
+    const int lane = threadIdx.x & 31;
+    const int k = lane / L, s = lane % L;
+    const int4 mt = *reinterpret_cast<const int4 *>(slot);
+    const BlobLayout<T> lay(mt.y, mt.z, L);
+    const bool active = k < mt.y;
+    T acc = T(0), dg = T(1), dy = T(1);
+    int32_t r = 0;
+    bool bail = false;
+    if (active && s == 0) {
+        r = reinterpret_cast<const int32_t *>(slot + 16 * lay.rows)[k];
+        const T *sd = reinterpret_cast<const T *>(slot + 16 * lay.diag) + 2 * k;
+        dg = sd[0];
+        dy = sd[1];
+        acc = (T)load_rhs(cx, (int64_t)r * cx.ld);
+    }
+    const int stride = mt.y * L;
+    const int32_t *scol = reinterpret_cast<const int32_t *>(slot + 16 * lay.cols) + k * L + s;
+    const T *sval = reinterpret_cast<const T *>(slot + 16 * lay.vals) + k * L + s;
+    // every step of the row in as few batches as possible: batches of 5
+    // (more spill at 64 registers), the remainder in one batch of its
+    // exact size; the first batch issued carries the refill
+    bool hook_pending = true;
+    int j = 0;
+    if (active)
+        for (; j + 5 <= mt.z; j += 5)
+            staged_steps<T, 5>(scol + j * stride, sval + j * stride, stride, out, cx, acc,
+                                   bail, refill, hook_pending);
+    switch (active ? mt.z - j : 0) {
+#define SPTRSV_STEPS(UU)                                                                       \
+    case UU:                                                                                   \
+        staged_steps<T, UU>(scol + j * stride, sval + j * stride, stride, out, cx, acc,    \
+                                bail, refill, hook_pending);                                    \
+        break;
+    SPTRSV_STEPS(1) SPTRSV_STEPS(2) SPTRSV_STEPS(3) SPTRSV_STEPS(4)
+#undef SPTRSV_STEPS
+    default: break;
+    }
+    if (hook_pending) refill();   // lanes without entries (inactive rows, empty rows)
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
+    if (active && s == 0) store_x<T, true>(out + (int64_t)r * cx.ld, div_by_diag<T>(acc, dg, dy));
+    return __any_sync(FULL_MASK, bail);
+}
+
+// Blob units [u0, u1) of chunk c (empty for c < 0).
+template <typename T>
+__device__ __forceinline__ void blob_range(const SolveData<T> &sd, int32_t c, int64_t &u0,
+                                           int64_t &u1) {
+    if (c < 0) {
+        u0 = u1 = 0;
+        return;
+    }
+    u0 = __ldg(sd.bofs + c);
+    u1 = __ldg(sd.bofs + c + 1);
+}
+
+// Prologue of both staged kernels: the ring's barriers, and the copies of
+// the warp's first two chunks into slots 0 and 1.
+template <typename T>
+__device__ __forceinline__ void ring_start(const SolveData<T> &sd, const StageRing<T> &ring,
+                                           int32_t c0, int32_t c1) {
+    if ((threadIdx.x & 31) == 0) {
+        for (int sl = 0; sl < kStageSlots; ++sl) mbar_init(ring.bar(sl), 32);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    int64_t u0, u1;
+    blob_range(sd, c0, u0, u1);
+    ring.fill(sd, 0, c0, u0, u1);
+    blob_range(sd, c1, u0, u1);
+    ring.fill(sd, 1, c1, u0, u1);
+}
+
+// After an abort: copies still in flight land before the CTA exits -- the
+// current slot's (chunk c) if it was never seen complete, and those of the
+// next two chunks cn1, cn2 (when their copies were started).
+template <typename T>
+__device__ __forceinline__ void ring_drain(const StageRing<T> &ring, int cur, int32_t c,
+                                           int32_t cn1, int32_t cn2, bool cur_unwaited,
+                                           uint32_t phase, uint64_t timeout_ns) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0 && c >= 0) {
+        for (int k = 0; k < kStageSlots; ++k) {
+            const int sl = (cur + k) % kStageSlots;
+            const int32_t cs = k == 0 ? c : k == 1 ? cn1 : cn2;
+            if (cs >= 0 && ring.staged(sl) && ring.hdr(sl)->x == cs && (k != 0 || cur_unwaited))
+                mbar_drain(ring.bar(sl), (phase >> sl) & 1u, timeout_ns);
+        }
+    }
+    __syncwarp();
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(kMaxSolveThreads, 2)
+solve_staged_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, DevStatus *st,
+                    uint64_t timeout_ns, int skip_if_converged) {
+    if (skip_if_converged && converged(st)) return;
+    extern __shared__ __align__(128) unsigned char stage_smem[];
+    const Ctx cx{rhs, ld, 1, st, timeout_ns, sd.backoff_ns, false, sd.n, sd.row_id, nullptr, 0};
+    const int wpb = blockDim.x >> 5, wib = threadIdx.x >> 5;
+    const int32_t gw = blockIdx.x * wpb + wib;
+    const int32_t nw = gridDim.x * wpb;
+    const StageRing<T> ring{stage_smem + (size_t)wib * stage_warp_bytes<T>(L, sd.stage_z),
+                            stage_slot_units<T>(L, sd.stage_z)};
+    const WarpChunks wc = warp_chunks(sd, gw, nw);
+    // the warp's current chunk and the next two; the ring holds the current
+    // one and the next, the chunk two ahead goes into the third slot while
+    // the current one runs
+    int32_t c = wc.at(0), cn1 = wc.at(1), cn2 = wc.at(2);
+    ring_start(sd, ring, c, cn1);
+    int64_t u2a, u2b;
+    blob_range(sd, cn2, u2a, u2b);
+    l2_prefetch_slice(sd.bofs, ((size_t)sd.nchunks + 1) * sizeof(int64_t));
+    if (sd.n > 0) {
+        size_t rb = ((size_t)(sd.n - 1) * ld + 1) * sizeof(double);
+        if (rb > (64u << 20)) rb = 64u << 20;
+        l2_prefetch_slice(rhs, rb);
+    }
+    // every unknown starts as the "not computed" sentinel; one grid barrier
+    // orders those stores before any poll (the copies above fly meanwhile)
+    {
+        const int32_t gthreads = gridDim.x * blockDim.x;
+        for (int32_t row = blockIdx.x * blockDim.x + threadIdx.x; row < sd.n; row += gthreads)
+            *reinterpret_cast<typename Bits<T>::U *>(out + (int64_t)row * ld) = Sentinel<T>::bits;
+    }
+    const bool ok = grid_barrier(st, gridDim.x, timeout_ns, -5);
+    // Each warp solves its chunks in order (the progress argument of
+    // solve_syncfree_kernel holds for both schedules; the copies a chunk
+    // waits for depend on nothing but the structure).
+    uint32_t phase = 0;   // bit s: parity of slot s's next completion
+    int cur = 0;
+    bool cur_unwaited = !ok;   // the current slot's copy was never seen complete
+    if (!ok) cn2 = -1;         // the third slot was never filled
+    for (int32_t j = 3; ok && c >= 0; ++j) {
+        const int32_t cn3 = wc.at(j);   // in flight while this chunk runs
+        const int nxt2 = cur == 0 ? 2 : cur - 1;   // (cur + 2) mod 3: the slot freed last
+        const Refill<T> refill{sd, ring, nxt2, cn2, u2a, u2b};
+        bool bail;
+        if (ring.staged(cur)) {
+            if (!__all_sync(FULL_MASK, mbar_wait(ring.bar(cur), (phase >> cur) & 1u, st,
+                                                 timeout_ns, -6))) {
+                cur_unwaited = true;
+                cn2 = -1;   // its copies were not started
+                break;
+            }
+            phase ^= 1u << cur;
+            bail = chunk_staged<T, L>(ring.slot(cur), out, cx, refill);
+        } else {
+            refill();
+            bail = chunk_one<T, L, true>(sd, c, out, cx);
+        }
+        if (bail) break;
+        __syncwarp();
+        blob_range(sd, cn3, u2a, u2b);
+        c = cn1;
+        cn1 = cn2;
+        cn2 = cn3;
+        cur = cur == kStageSlots - 1 ? 0 : cur + 1;
+    }
+    ring_drain(ring, cur, c, cn1, cn2, cur_unwaited, phase, timeout_ns);
+    grid_exit(st);
+}
+
+template <typename T>
+const void *pick_staged(int L) {
+    switch (L) {
+    case 1: return (const void *)solve_staged_kernel<T, 1>;
+    case 2: return (const void *)solve_staged_kernel<T, 2>;
+    case 4: return (const void *)solve_staged_kernel<T, 4>;
+    case 8: return (const void *)solve_staged_kernel<T, 8>;
+    case 16: return (const void *)solve_staged_kernel<T, 16>;
+    case 32: return (const void *)solve_staged_kernel<T, 32>;
+    }
+    return nullptr;
+}
+
+template <typename T>
+size_t stage_smem_bytes(int L, int stage_z, int block_threads) {
+    return stage_z > 0 ? (size_t)(block_threads / 32) * stage_warp_bytes<T>(L, stage_z) : 0;
+}
+
+
+
 
 template <typename T, bool SF, int R>
 const void *pick_l(int L) {
@@ -864,6 +1208,85 @@ batch_kernel(const BatchMat *__restrict__ mats, int32_t nmats, BatchCtl *ctl, De
 }
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Chunk blobs (BlobLayout) of a solve structure.
+namespace {
+template <typename T>
+__global__ void blob_units_kernel(int32_t nchunks, int L, const int4 *__restrict__ meta,
+                                  int64_t *units) {
+    const int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nchunks) return;
+    const int4 m = meta[c];
+    units[c] = BlobLayout<T>(m.y, m.z, L).units;
+}
+
+// one warp per chunk; the blob array is zeroed beforehand (padding)
+template <typename T>
+__global__ void blob_fill_kernel(int32_t nchunks, int L, const int4 *__restrict__ meta,
+                                 const int32_t *__restrict__ row_id, const T *__restrict__ diag,
+                                 const int32_t *__restrict__ ecol, const T *__restrict__ eval,
+                                 const int64_t *__restrict__ bofs, uint4 *blob) {
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= nchunks) return;
+    const int4 m = meta[c];
+    const BlobLayout<T> lay(m.y, m.z, L);
+    unsigned char *base = reinterpret_cast<unsigned char *>(blob + bofs[c]);
+    if (lane == 0) *reinterpret_cast<int4 *>(base) = m;
+    int32_t *rows = reinterpret_cast<int32_t *>(base + 16 * lay.rows);
+    T *dg = reinterpret_cast<T *>(base + 16 * lay.diag);
+    int32_t *cols = reinterpret_cast<int32_t *>(base + 16 * lay.cols);
+    T *vals = reinterpret_cast<T *>(base + 16 * lay.vals);
+    for (int k = lane; k < m.y; k += 32) rows[k] = row_id[m.x + k];
+    for (int e = lane; e < 2 * m.y; e += 32) dg[e] = diag[2 * (int64_t)m.x + e];
+    const int ne = m.z * m.y * L;
+    for (int e = lane; e < ne; e += 32) {
+        cols[e] = ecol[(int64_t)m.w + e];
+        vals[e] = eval[(int64_t)m.w + e];
+    }
+}
+}  // namespace
+
+template <typename T>
+cudaError_t launch_blob_units(int32_t nchunks, int L, const int4 *meta, int64_t *units,
+                              cudaStream_t s) {
+    if (nchunks <= 0) return cudaSuccess;
+    blob_units_kernel<T><<<(nchunks + 255) / 256, 256, 0, s>>>(nchunks, L, meta, units);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_blob_fill(int32_t nchunks, int L, const int4 *meta, const int32_t *row_id,
+                             const T *diag, const int32_t *ecol, const T *eval,
+                             const int64_t *bofs, uint4 *blob, cudaStream_t s) {
+    if (nchunks <= 0) return cudaSuccess;
+    const int64_t threads = (int64_t)nchunks * 32;
+    blob_fill_kernel<T><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+        nchunks, L, meta, row_id, diag, ecol, eval, bofs, blob);
+    return cudaGetLastError();
+}
+template cudaError_t launch_blob_units<double>(int32_t, int, const int4 *, int64_t *,
+                                               cudaStream_t);
+template cudaError_t launch_blob_units<float>(int32_t, int, const int4 *, int64_t *,
+                                              cudaStream_t);
+template cudaError_t launch_blob_fill<double>(int32_t, int, const int4 *, const int32_t *,
+                                              const double *, const int32_t *, const double *,
+                                              const int64_t *, uint4 *, cudaStream_t);
+template cudaError_t launch_blob_fill<float>(int32_t, int, const int4 *, const int32_t *,
+                                             const float *, const int32_t *, const float *,
+                                             const int64_t *, uint4 *, cudaStream_t);
+
+template <typename T>
+int stage_cap_z(int L, int smem_per_sm, int warps) {
+    int z = 0;
+    // 1 KiB reserved per CTA: up to 8 CTAs (blocks of 128 threads) per SM
+    const int budget = smem_per_sm - 8 * 1024;
+    for (int c = 1; c <= kStageZMax; ++c)
+        if (warps * stage_warp_bytes<T>(L, c) <= budget) z = c;
+    return z;
+}
+template int stage_cap_z<double>(int, int, int);
+template int stage_cap_z<float>(int, int, int);
+
 int batch_max_coresident(bool ir, int block_threads, int num_sms) {
     int per_sm = 0;
     const void *k = ir ? (const void *)batch_kernel<true> : (const void *)batch_kernel<false>;
@@ -897,24 +1320,38 @@ size_t run_smem_bytes(int nr, bool syncfree, int run_slots) {
     return (!syncfree && nr <= 1 && run_slots > 0) ? (size_t)run_slots * sizeof(T) : 0;
 }
 
+// The kernel a launch runs, its block size and dynamic shared memory.
+struct KernelPick {
+    const void *k;
+    int block;
+    size_t smem;
+};
+template <typename T>
+KernelPick choose_kernel(int L, int nr, bool syncfree, int block_threads, int run_slots,
+                         int stage_z) {
+    const int bt = block_threads < kMaxSolveThreads ? block_threads : kMaxSolveThreads;
+    if (syncfree && nr <= 1 && stage_z > 0)
+        return {pick_staged<T>(L), bt, stage_smem_bytes<T>(L, stage_z, bt)};
+    return {pick_kernel<T>(L, nr, syncfree), bt, run_smem_bytes<T>(nr, syncfree, run_slots)};
+}
+
 template <typename T>
 int max_coresident_ctas(int L, int nr, bool syncfree, int block_threads, int num_sms,
-                        int run_slots) {
-    const void *k = pick_kernel<T>(L, nr, syncfree);
-    if (!k) return 0;
-    const size_t smem = run_smem_bytes<T>(nr, syncfree, run_slots);
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                        int run_slots, int stage_z) {
+    const KernelPick kp = choose_kernel<T>(L, nr, syncfree, block_threads, run_slots, stage_z);
+    if (!kp.k) return 0;
+    if (kp.smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kp.k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kp.smem) !=
             cudaSuccess)
         return 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block_threads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kp.k, kp.block, kp.smem) !=
         cudaSuccess)
         return 0;
     return per_sm * num_sms;
 }
-template int max_coresident_ctas<double>(int, int, bool, int, int, int);
-template int max_coresident_ctas<float>(int, int, bool, int, int, int);
+template int max_coresident_ctas<double>(int, int, bool, int, int, int, int);
+template int max_coresident_ctas<float>(int, int, bool, int, int, int, int);
 
 template <typename T>
 cudaError_t launch_solve(const SolveData<T> &sd, const double *rhs, T *out, int32_t n,
@@ -922,17 +1359,24 @@ cudaError_t launch_solve(const SolveData<T> &sd, const double *rhs, T *out, int3
                          DevStatus *st, uint64_t timeout_ns, bool skip_if_converged,
                          cudaStream_t s) {
     if (n == 0 || nr == 0) return cudaSuccess;
-    const void *k = pick_kernel<T>(sd.L, nr, syncfree);
+    if (sd.stage_z < 0 || sd.stage_z > kStageZMax) return cudaErrorInvalidValue;
+    SolveData<T> sdc = sd;
+    if (!sdc.blob || !sdc.bofs) sdc.stage_z = 0;   // no blobs: the unstaged kernels
+    const KernelPick kp = choose_kernel<T>(sdc.L, nr, syncfree, cfg.block_threads,
+                                           sdc.run_slots, sdc.stage_z);
+    const bool staged = syncfree && nr == 1 && sdc.stage_z > 0;
+    const void *k = kp.k;
     if (!k) return cudaErrorInvalidValue;
     const int skip = skip_if_converged ? 1 : 0;
-    SolveData<T> sdc = sd;
     void *args[] = {(void *)&sdc, (void *)&rhs,        (void *)&out,  (void *)&ld,
                     (void *)&nr,  (void *)&st,         (void *)&timeout_ns,
                     (void *)&skip};
+    void *sargs[] = {(void *)&sdc, (void *)&rhs, (void *)&out, (void *)&ld,
+                     (void *)&st,  (void *)&timeout_ns, (void *)&skip};
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(cfg.grid);
-    lc.blockDim = dim3(cfg.block_threads);
-    lc.dynamicSmemBytes = run_smem_bytes<T>(nr, syncfree, sd.run_slots);
+    lc.blockDim = dim3(kp.block);
+    lc.dynamicSmemBytes = kp.smem;
     if (lc.dynamicSmemBytes > 48 * 1024) {
         cudaError_t ea = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)lc.dynamicSmemBytes);
@@ -944,7 +1388,7 @@ cudaError_t launch_solve(const SolveData<T> &sd, const double *rhs, T *out, int3
     attr[0].val.cooperative = 1;
     lc.attrs = attr;
     lc.numAttrs = 1;
-    return cudaLaunchKernelExC(&lc, k, args);
+    return cudaLaunchKernelExC(&lc, k, staged ? sargs : args);
 }
 template cudaError_t launch_solve<double>(const SolveData<double> &, const double *, double *,
                                           int32_t, int, int, bool, const LaunchCfg &,

@@ -33,7 +33,61 @@ struct SolveData {
     // col = -(n + 1) - slot, slot = solve position - first position of the
     // run; run_slots = largest run (rows), 0 when there are no runs.
     int32_t run_slots;
+    // Staging of the synchronisation-free solve (one right-hand side): chunks
+    // of at most stage_z steps per lane are copied into shared memory by the
+    // bulk-copy engine one chunk ahead; 0 = no staging.  row_id must hold 4
+    // spare elements past n and diag 8 (aligned over-reads of the copies).
+    int32_t stage_z;
+    // Chunk schedule of the synchronisation-free kernels for a grid of
+    // sched_nw warps: warp w solves sched[sched_ptr[w] .. sched_ptr[w + 1])
+    // in that order (level by level, the level's chunks dealt out to warps
+    // 0, 1, ... in turn).  Null, or another warp count: chunk c goes to warp
+    // c mod (warps), in chunk order.
+    const int32_t *sched;
+    const int32_t *sched_ptr;
+    int32_t sched_nw;
+    // Chunk blobs of the staged kernels (BlobLayout): chunk c occupies the
+    // 16-byte units [bofs[c], bofs[c + 1]) of blob.
+    const uint4 *blob;
+    const int64_t *bofs;
 };
+
+// One chunk as one contiguous run of 16-byte units: unit 0 the chunk
+// descriptor (first position, rows y, steps z, entry offset), then the row
+// ids (y int32), the diagonal pairs (2y elements), the columns (z y L int32,
+// in the entry order of ecol) and the values (z y L elements), each padded
+// to whole units.
+template <typename T>
+struct BlobLayout {
+    int rows, diag, cols, vals, units;   // unit offsets, total units
+    __host__ __device__ BlobLayout(int y, int z, int L) {
+        const int ne = z * y * L;
+        rows = 1;
+        diag = rows + (4 * y + 15) / 16;
+        cols = diag + (2 * y * (int)sizeof(T) + 15) / 16;
+        vals = cols + (4 * ne + 15) / 16;
+        units = vals + ((int)sizeof(T) * ne + 15) / 16;
+    }
+};
+
+// Builds the blobs of a structure: bofs[nchunks + 1] (exclusive prefix of
+// the chunks' units, computed here) and blob (units: bofs[nchunks]); the
+// caller allocates blob after reading the total (two phases).
+template <typename T>
+cudaError_t launch_blob_units(int32_t nchunks, int L, const int4 *meta, int64_t *units,
+                              cudaStream_t s);
+template <typename T>
+cudaError_t launch_blob_fill(int32_t nchunks, int L, const int4 *meta, const int32_t *row_id,
+                             const T *diag, const int32_t *ecol, const T *eval,
+                             const int64_t *bofs, uint4 *blob, cudaStream_t s);
+
+// Largest staging width (steps per lane) the kernels accept.
+constexpr int kStageZMax = 12;
+// Largest staging width whose slots, for `warps` resident warps of the
+// layout with L lanes per row, fit in `smem_per_sm` bytes of shared memory
+// (with 1 KiB per CTA reserved).
+template <typename T>
+int stage_cap_z(int L, int smem_per_sm, int warps);
 
 struct LaunchCfg {
     int block_threads;   // threads per CTA
@@ -55,7 +109,7 @@ cudaError_t launch_solve(const SolveData<T> &sd, const double *rhs, T *out, int3
 // the dynamic shared memory the barrier kernel's runs need.
 template <typename T>
 int max_coresident_ctas(int L, int nr, bool syncfree, int block_threads, int num_sms,
-                        int run_slots = 0);
+                        int run_slots = 0, int stage_z = 0);
 
 // ---------------------------------------------------------------------------
 // Batched solve: many independent plans in one persistent launch.  Matrix m

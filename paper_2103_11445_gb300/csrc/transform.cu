@@ -290,7 +290,8 @@ __global__ void chunk_width_kernel(int32_t nchunks, const int32_t *__restrict__ 
         w = s > w ? s : w;
     }
     width_out[c] = w;
-    slots[c] = (int64_t)w * nr * L;
+    // a multiple of 4 entries: chunks start on 16-byte boundaries
+    slots[c] = ((int64_t)w * nr * L + 3) & ~(int64_t)3;
 }
 
 // one thread per (chunk, row-in-chunk): writes the row's entries and pads

@@ -221,3 +221,30 @@ def test_pcg_rejects_bad_matrices():
     with pytest.raises(B.SptrsvError) as ei:
         B.PCG(0, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
     assert ei.value.code == 1
+
+
+def test_pcg_breakdown_is_reported():
+    """A NaN in the starting guess, and a symmetric indefinite matrix under the
+    symmetric Gauss-Seidel preconditioner, end with SPTRSV_ERR_BREAKDOWN
+    instead of a converged-looking garbage x."""
+    import torch
+    from paper_2103_11445_gb300 import binding as B
+    A = mg.symmetric_from_lower(mg.stencil2d(9))
+    G = B.PCG(A.n, A.row_ptr, A.col, A.val)
+    b = torch.as_tensor(mg.rhs_uniform(A.n, seed=4), device="cuda")
+    x0 = torch.zeros_like(b)
+    x0[5] = float("nan")
+    with pytest.raises(B.SptrsvError) as ei:
+        G.solve(b, x0)
+    assert ei.value.code == 11
+    x, it, rel = G.solve(b, rtol=1e-10)                 # the object is still usable
+    assert rel <= 1e-10 and it > 0
+    G.close()
+    # diag(1, -1), b = (1, 2): z = M^-1 r = (1, -2), so (p, A p) = 1 - 4 < 0
+    D = mg.CSR(2, np.array([0, 1, 2], np.int32), np.array([0, 1], np.int32),
+               np.array([1.0, -1.0]))
+    G = B.PCG(2, D.row_ptr, D.col, D.val)
+    with pytest.raises(B.SptrsvError) as ei:
+        G.solve(torch.tensor([1.0, 2.0], dtype=torch.float64, device="cuda"))
+    assert ei.value.code == 11
+    G.close()

@@ -15,8 +15,8 @@ TOL64 = 1e-10   # relerr bound for FP64 results
 TOL32 = 1e-5    # relerr bound for unrefined FP32 results
 
 B_MODES = [dict(solve_mode=1, cta_run_rows=-1), dict(solve_mode=1, cta_run_rows=0),
-           dict(solve_mode=2)]
-B_IDS = ["barrier", "barrier_runs", "syncfree"]
+           dict(solve_mode=2), dict(solve_mode=2, stage_z=-1)]
+B_IDS = ["barrier", "barrier_runs", "syncfree", "syncfree_unstaged"]
 
 
 def plain(**kw):

@@ -126,3 +126,34 @@ def test_autotuner_considers_the_tail():
     P.check()
     assert oracle.relerr(x.cpu().numpy(), oracle.forward_subst(A, b)) <= TOL64
     P.close()
+
+
+def test_injected_wait_in_the_tail_times_out():
+    """The failure-detection hook on a row that the single-CTA tail would
+    solve: the tail (which does not wait) is switched off for good, so the
+    bounded wait of the main kernel reports TIMEOUT.  A transform after the
+    injection rebuilds the structure from the matrix (the injected
+    dependency is gone: the solve is right again) and keeps the tail off."""
+    import torch
+    from paper_2103_11445_gb300 import binding as B
+    A = mg.thin_tail(20_000, seed=3100)
+    kw = dict(select_mode=0, solve_mode=2, tail_rows=32, wait_timeout_ms=200)
+    b = mg.rhs_uniform(A.n, seed=4)
+    bt = torch.as_tensor(b, device="cuda")
+    P = B.Plan(A.n, A.row_ptr, A.col, A.val)
+    P.transform(**kw)
+    assert P.info()["tail_levels"] > 0
+    B.sptrsv_debug_inject_wait(P.handle, A.n - 3)
+    assert P.info()["tail_levels"] == 0
+    P.solve(bt)
+    assert B.sptrsv_check(P.handle, 0) == 8   # SPTRSV_ERR_TIMEOUT
+    P.close()
+    Q = B.Plan(A.n, A.row_ptr, A.col, A.val)
+    Q.transform(**kw)
+    B.sptrsv_debug_inject_wait(Q.handle, A.n - 3)
+    Q.transform(**kw)
+    assert Q.info()["tail_levels"] == 0
+    x = Q.solve(bt)
+    Q.check()
+    assert oracle.relerr(x.cpu().numpy(), oracle.forward_subst(A, b)) <= TOL64
+    Q.close()
