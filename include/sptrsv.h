@@ -78,10 +78,23 @@ typedef void *sptrsv_stream_t;                  /* cudaStream_t */
 enum {
     SPTRSV_SELECT_NONE = 0,       /* plain level sets, nothing rewritten */
     SPTRSV_SELECT_HEURISTIC = 1,  /* thin-level heuristic H (below) */
-    SPTRSV_SELECT_COSTMODEL = 2,  /* learned cost model picks the depth per
-                                     segment; needs sptrsv_set_costmodel */
-    SPTRSV_SELECT_FIXED = 3       /* merge every `depth`+1 consecutive levels */
+    SPTRSV_SELECT_COSTMODEL = 2,  /* learned cost model picks the rewrite
+                                     (sptrsv_set_costmodel or
+                                     sptrsv_costmodel_load; else H) */
+    SPTRSV_SELECT_FIXED = 3,      /* merge every `depth`+1 consecutive levels */
+    SPTRSV_SELECT_AUTO = 4        /* measured: times the candidates below on
+                                     the plan and keeps the fastest */
 };
+/* SPTRSV_SELECT_AUTO: the candidates are the plain level sets (code 0),
+ * merging every d+1 levels for d = 1, 2, 3 (code d), heuristic H with the
+ * given thin_rows / max_depth / flop_budget (code 200), H on the levels of
+ * fewer than 32 rows, up to 8 or 16 deep, within 4x the plain FLOPs (codes
+ * 108, 116), and the cost model's pick when a network is available (its
+ * code).  Each is built and timed with the synchronisation-free kernel at 1
+ * and at 4 lanes per row (one warm-up and three solves of a vector of ones,
+ * the fastest counts); the fastest candidate is then transformed with the
+ * caller's solve_mode (SOLVE_AUTO: launch autotuning as usual).
+ * sptrsv_info_t.chosen_depth is its code; transform_ms covers the search. */
 /* Solve kernels.  BARRIER: persistent grid, one grid barrier per level (or
  * per run of thin levels kept inside one CTA).  SYNCFREE: no barriers, each
  * row waits for the unknowns it reads (Sec. II).  AUTO: the autotuner times
@@ -285,7 +298,8 @@ SPTRSV_API sptrsv_status_t sptrsv_get_transformed(sptrsv_plan_t p, int32_t *d_ne
 
 /* ---- Learned cost model ----------------------------------------------
  * The paper picks the rows to rewrite by hand (Sec. IV).  With a network
- * attached (sptrsv_set_costmodel), SPTRSV_SELECT_COSTMODEL predicts the log
+ * attached (sptrsv_set_costmodel, or the process-wide one of
+ * sptrsv_costmodel_load), SPTRSV_SELECT_COSTMODEL predicts the log
  * solve time of every candidate rewrite from 17 features per candidate and
  * keeps the argmin; without one it falls back to heuristic H.  Candidates
  * (codes): d in {0,1,2,3,4,6,8} merges every d+1 levels (0 = plain level
@@ -331,6 +345,43 @@ SPTRSV_API sptrsv_status_t sptrsv_mlp_train_step(sptrsv_mlp_t net, const float *
                                                  const float *d_target, int32_t N, float lr,
                                                  float *d_loss, sptrsv_stream_t stream);
 SPTRSV_API void sptrsv_mlp_destroy(sptrsv_mlp_t net);
+
+/* Input normalisation computed by the library (training data stay on the
+ * device; no host arithmetic): sptrsv_mlp_fit_normalization sets the
+ * network's statistics to the column means and standard deviations of
+ * d_X[N][F] (FP64 sums in a fixed order; a deviation below 1e-6 is taken as
+ * 1) and synchronises `stream`; sptrsv_mlp_normalize writes
+ * d_Xn = (d_X - mean) / std (d_Xn may equal d_X) and synchronises;
+ * sptrsv_mlp_get_normalization copies the statistics out (mean 0, std 1
+ * before any are set). */
+SPTRSV_API sptrsv_status_t sptrsv_mlp_fit_normalization(sptrsv_mlp_t net, const float *d_X,
+                                                        int32_t N, sptrsv_stream_t stream);
+SPTRSV_API sptrsv_status_t sptrsv_mlp_normalize(sptrsv_mlp_t net, const float *d_X, int32_t N,
+                                                float *d_Xn, sptrsv_stream_t stream);
+SPTRSV_API sptrsv_status_t sptrsv_mlp_get_normalization(sptrsv_mlp_t net, float *h_mean,
+                                                        float *h_std);
+
+/* Network files.  Layout (little-endian): the 8 bytes "SPTRSVNN"; int32
+ * version (1), F, H, has_normalisation; float32 weights (the flat layout
+ * above, sptrsv_mlp_num_params(F, H) of them); float32 mean[F]; float32
+ * std[F]; nothing after.  sptrsv_mlp_save writes a network (synchronises the
+ * device copy of its weights); sptrsv_mlp_load creates a new network from a
+ * file (SPTRSV_ERR_INVALID_ARG for a missing, short, long or foreign file).
+ * Adam's moments are not saved: a loaded network trains from fresh moments. */
+SPTRSV_API sptrsv_status_t sptrsv_mlp_save(sptrsv_mlp_t net, const char *path);
+SPTRSV_API sptrsv_status_t sptrsv_mlp_load(const char *path, sptrsv_mlp_t *out);
+
+/* The process-wide cost model: SPTRSV_SELECT_COSTMODEL uses a plan's own
+ * network (sptrsv_set_costmodel) if attached, else this one, else heuristic
+ * H.  sptrsv_costmodel_load reads a network file into it (owned by the
+ * library, replacing and freeing an earlier loaded one); sptrsv_costmodel_save
+ * writes it (SPTRSV_ERR_BAD_STATE when there is none);
+ * sptrsv_costmodel_set_default makes a caller-owned network the default (NULL
+ * clears it; destroying that network also clears it).  Not to be called
+ * while a transform runs in another thread. */
+SPTRSV_API sptrsv_status_t sptrsv_costmodel_load(const char *path);
+SPTRSV_API sptrsv_status_t sptrsv_costmodel_save(const char *path);
+SPTRSV_API sptrsv_status_t sptrsv_costmodel_set_default(sptrsv_mlp_t net);
 
 /* Batched solve (the paper treats one matrix; this serves many independent
  * systems of uneven size at once).  All plans must live on the current

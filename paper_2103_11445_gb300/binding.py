@@ -24,7 +24,7 @@ STATUS_NAMES = {
     5: "MISSING_DIAG", 6: "OOM", 7: "CUDA", 8: "TIMEOUT", 9: "BAD_STATE",
     10: "UNSUPPORTED", 11: "BREAKDOWN",
 }
-SELECT_NONE, SELECT_HEURISTIC, SELECT_COSTMODEL, SELECT_FIXED = 0, 1, 2, 3
+SELECT_NONE, SELECT_HEURISTIC, SELECT_COSTMODEL, SELECT_FIXED, SELECT_AUTO = 0, 1, 2, 3, 4
 SOLVE_AUTO, SOLVE_BARRIER, SOLVE_SYNCFREE = 0, 1, 2
 F64, F32_IR = 0, 1
 OP_LOWER, OP_UPPER, OP_LOWER_TRANS, OP_UPPER_TRANS = 0, 1, 2, 3
@@ -106,6 +106,14 @@ _SIGS = {
     "sptrsv_mlp_train_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, ctypes.c_float,
                                         c_void_p, c_void_p]),
     "sptrsv_mlp_destroy": (None, [c_void_p]),
+    "sptrsv_mlp_fit_normalization": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p]),
+    "sptrsv_mlp_normalize": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
+    "sptrsv_mlp_get_normalization": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "sptrsv_mlp_save": (c_int32, [c_void_p, ctypes.c_char_p]),
+    "sptrsv_mlp_load": (c_int32, [ctypes.c_char_p, POINTER(c_void_p)]),
+    "sptrsv_costmodel_load": (c_int32, [ctypes.c_char_p]),
+    "sptrsv_costmodel_save": (c_int32, [ctypes.c_char_p]),
+    "sptrsv_costmodel_set_default": (c_int32, [c_void_p]),
     "sptrsv_batch_create": (c_int32, [c_void_p, c_int32, POINTER(c_void_p)]),
     "sptrsv_batch_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sptrsv_batch_check": (c_int32, [c_void_p, c_void_p]),
@@ -319,6 +327,46 @@ def sptrsv_mlp_train_step(mlp: int, d_X: int, d_t: int, N: int, lr: float, d_los
 def sptrsv_mlp_destroy(mlp: int) -> None:
     if mlp:
         load().sptrsv_mlp_destroy(mlp)
+
+
+def sptrsv_mlp_fit_normalization(mlp: int, d_X: int, N: int, stream: int = 0) -> None:
+    _check(load().sptrsv_mlp_fit_normalization(mlp, d_X, N, stream),
+           "sptrsv_mlp_fit_normalization")
+
+
+def sptrsv_mlp_normalize(mlp: int, d_X: int, N: int, d_Xn: int, stream: int = 0) -> None:
+    _check(load().sptrsv_mlp_normalize(mlp, d_X, N, d_Xn, stream), "sptrsv_mlp_normalize")
+
+
+def sptrsv_mlp_get_normalization(mlp: int, n_in: int):
+    import numpy as np
+    mean = np.zeros(n_in, dtype=np.float32)
+    std = np.zeros(n_in, dtype=np.float32)
+    _check(load().sptrsv_mlp_get_normalization(mlp, mean.ctypes.data, std.ctypes.data),
+           "sptrsv_mlp_get_normalization")
+    return mean, std
+
+
+def sptrsv_mlp_save(mlp: int, path: str) -> None:
+    _check(load().sptrsv_mlp_save(mlp, os.fsencode(path)), "sptrsv_mlp_save")
+
+
+def sptrsv_mlp_load(path: str) -> int:
+    out = c_void_p()
+    _check(load().sptrsv_mlp_load(os.fsencode(path), byref(out)), "sptrsv_mlp_load")
+    return out.value
+
+
+def sptrsv_costmodel_load(path: str) -> None:
+    _check(load().sptrsv_costmodel_load(os.fsencode(path)), "sptrsv_costmodel_load")
+
+
+def sptrsv_costmodel_save(path: str) -> None:
+    _check(load().sptrsv_costmodel_save(os.fsencode(path)), "sptrsv_costmodel_save")
+
+
+def sptrsv_costmodel_set_default(mlp: int) -> None:
+    _check(load().sptrsv_costmodel_set_default(mlp), "sptrsv_costmodel_set_default")
 
 
 def sptrsv_batch_create(plans) -> int:

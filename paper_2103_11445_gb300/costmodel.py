@@ -37,6 +37,8 @@ THIN_BUDGET = 4.0
 N_FEATURES = 17
 HIDDEN = 64
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "costmodel_weights.npz")
+# the same network in the library's file format (sptrsv_costmodel_load)
+WEIGHTS_BIN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "costmodel_weights.bin")
 # Launch shapes of the timing labels: a label is the fastest of these
 # (sync-free kernel, 128 threads per CTA): one lane per row on one CTA per
 # SM, and four lanes per row on four CTAs per SM -- between them the shapes
@@ -59,30 +61,51 @@ def init_params(n_in: int = N_FEATURES, hidden: int = HIDDEN, seed: int = 0) -> 
 
 
 class CostModel:
-    """A cost-model network living on the current CUDA device."""
+    """A cost-model network living on the current CUDA device.  Feature
+    standardisation is the library's (sptrsv_mlp_fit_normalization /
+    sptrsv_mlp_normalize): features go to the device as they are."""
 
     def __init__(self, params: np.ndarray | None = None, mean=None, std=None,
-                 n_in: int = N_FEATURES, hidden: int = HIDDEN, seed: int = 0):
+                 n_in: int = N_FEATURES, hidden: int = HIDDEN, seed: int = 0,
+                 handle: int = 0):
         self.n_in, self.hidden = n_in, hidden
+        if handle:
+            self.handle = handle
+            return
         if params is None:
             params = init_params(n_in, hidden, seed)
         self.handle = B.sptrsv_mlp_create(n_in, hidden, params)
-        self.mean = np.zeros(n_in, np.float32) if mean is None else np.asarray(mean, np.float32)
-        self.std = np.ones(n_in, np.float32) if std is None else np.asarray(std, np.float32)
-        B.sptrsv_mlp_set_normalization(self.handle, self.mean, self.std)
+        if mean is not None and std is not None:
+            B.sptrsv_mlp_set_normalization(self.handle, np.asarray(mean, np.float32),
+                                           np.asarray(std, np.float32))
+
+    @property
+    def mean(self) -> np.ndarray:
+        return B.sptrsv_mlp_get_normalization(self.handle, self.n_in)[0]
+
+    @property
+    def std(self) -> np.ndarray:
+        return B.sptrsv_mlp_get_normalization(self.handle, self.n_in)[1]
+
+    def _normalised(self, X: np.ndarray, fit: bool = False):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        Xd = torch.as_tensor(np.ascontiguousarray(X, dtype=np.float32), device=dev)
+        stream = torch.cuda.current_stream().cuda_stream
+        if fit:
+            B.sptrsv_mlp_fit_normalization(self.handle, Xd.data_ptr(), Xd.shape[0], stream)
+        B.sptrsv_mlp_normalize(self.handle, Xd.data_ptr(), Xd.shape[0], Xd.data_ptr(), stream)
+        return Xd
 
     # -- training ----------------------------------------------------------
     def fit(self, X: np.ndarray, y: np.ndarray, epochs: int = 3000, lr: float = 3e-3,
             log_every: int = 0) -> list:
-        """Full-batch Adam on normalised features (statistics from X)."""
+        """Full-batch Adam on features standardised by the library (statistics
+        from X, computed on the device)."""
         import torch
-        self.mean = X.mean(axis=0).astype(np.float32)
-        self.std = np.where(X.std(axis=0) > 1e-6, X.std(axis=0), 1.0).astype(np.float32)
-        B.sptrsv_mlp_set_normalization(self.handle, self.mean, self.std)
-        dev = torch.device("cuda", torch.cuda.current_device())
-        Xn = torch.as_tensor((X - self.mean) / self.std, dtype=torch.float32, device=dev)
-        t = torch.as_tensor(y, dtype=torch.float32, device=dev)
-        loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        Xn = self._normalised(X, fit=True)
+        t = torch.as_tensor(y, dtype=torch.float32, device=Xn.device)
+        loss = torch.zeros(1, dtype=torch.float32, device=Xn.device)
         stream = torch.cuda.current_stream().cuda_stream
         hist = []
         for e in range(epochs):
@@ -94,10 +117,8 @@ class CostModel:
 
     def predict(self, X: np.ndarray) -> np.ndarray:
         import torch
-        dev = torch.device("cuda", torch.cuda.current_device())
-        Xn = torch.as_tensor((np.asarray(X) - self.mean) / self.std, dtype=torch.float32,
-                             device=dev)
-        y = torch.empty(Xn.shape[0], dtype=torch.float32, device=dev)
+        Xn = self._normalised(X)
+        y = torch.empty(Xn.shape[0], dtype=torch.float32, device=Xn.device)
         B.sptrsv_mlp_forward(self.handle, Xn.data_ptr(), Xn.shape[0], y.data_ptr(),
                              torch.cuda.current_stream().cuda_stream)
         return y.cpu().numpy()
@@ -107,11 +128,21 @@ class CostModel:
 
     # -- persistence ------------------------------------------------------------
     def save(self, path: str = WEIGHTS) -> None:
+        """The library's network file (sptrsv_mlp_save) for a path ending in
+        .bin, else an .npz archive with the same contents."""
+        if path.endswith(".bin"):
+            B.sptrsv_mlp_save(self.handle, path)
+            return
         np.savez(path, params=self.params(), mean=self.mean, std=self.std,
                  n_in=self.n_in, hidden=self.hidden, candidates=np.array(CANDIDATES))
 
     @classmethod
     def load(cls, path: str = WEIGHTS) -> "CostModel":
+        if path.endswith(".bin"):
+            import struct
+            with open(path, "rb") as fh:
+                _, n_in, hidden, _ = struct.unpack("<4i", fh.read(24)[8:])
+            return cls(n_in=n_in, hidden=hidden, handle=B.sptrsv_mlp_load(path))
         d = np.load(path)
         return cls(d["params"], d["mean"], d["std"], int(d["n_in"]), int(d["hidden"]))
 
@@ -232,9 +263,19 @@ def main(argv=None) -> int:
     t.add_argument("--lr", type=float, default=3e-3)
     t.add_argument("--extra", default=None,
                    help="additional training-only data (e.g. the larger matrices)")
+    x = sub.add_parser("export", help="write weights as the library's network file")
+    x.add_argument("--weights", default=WEIGHTS)
+    x.add_argument("--out", default=WEIGHTS_BIN)
     args = ap.parse_args(argv)
     import torch
     torch.cuda.set_device(0)
+    if args.cmd == "export":
+        m = CostModel.load(args.weights)
+        m.save(args.out)
+        q = CostModel.load(args.out)
+        assert np.array_equal(q.params(), m.params())
+        print(args.out)
+        return 0
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import matgen as mg
     if args.cmd == "collect":

@@ -18,6 +18,7 @@ using namespace sptrsv;
 
 namespace sptrsv {
 // mlp.cu: normalise h_feat [count][16] and run the network, h_pred[count]
+sptrsv_mlp_t default_costmodel();   // mlp.cu: the process-wide network, or null
 sptrsv_status_t costmodel_predict(sptrsv_mlp_t net, const float *h_feat, int count,
                                   float *h_pred, cudaStream_t s);
 }
@@ -287,13 +288,15 @@ sptrsv_status_t choose_segments(sptrsv_plan_t p, cudaStream_t s) {
     int64_t tau;
     int32_t d_max;
     double rho;
-    if (prm.select_mode == SPTRSV_SELECT_COSTMODEL && p->costmodel) {
+    // the plan's network, else the process-wide one (sptrsv_costmodel_load)
+    sptrsv_mlp_t net = p->costmodel ? p->costmodel : default_costmodel();
+    if (prm.select_mode == SPTRSV_SELECT_COSTMODEL && net) {
         // the network predicts the log solve time of every candidate depth
         float feat[kNumCostDepths * kCostFeatures];
         for (int i = 0; i < kNumCostDepths; ++i)
             CKS(candidate_features(p, kCostDepths[i], feat + i * kCostFeatures, s));
         float pred[kNumCostDepths];
-        CKS(costmodel_predict(p->costmodel, feat, kNumCostDepths, pred, s));
+        CKS(costmodel_predict(net, feat, kNumCostDepths, pred, s));
         int best = 0;
         for (int i = 1; i < kNumCostDepths; ++i)
             if (pred[i] < pred[best]) best = i;
@@ -1146,6 +1149,98 @@ sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t 
     return SPTRSV_OK;
 }
 
+// SPTRSV_SELECT_AUTO: every candidate rewrite is built and timed on the plan
+// (synchronisation-free kernel, 1 and 4 lanes per row), and the fastest one
+// is transformed with the caller's launch parameters.
+sptrsv_status_t select_auto(sptrsv_plan_t p, const sptrsv_transform_params_t *prm,
+                            sptrsv_stream_t stream) {
+    const double t0 = now_ms();
+    cudaStream_t s = (cudaStream_t)stream;
+    struct Cand {
+        int code;
+        sptrsv_transform_params_t q;
+    };
+    std::vector<Cand> cands;
+    auto add = [&](int code, int mode, int depth, int thin, int dmax, double rho) {
+        for (const Cand &c : cands)
+            if (c.code == code) return;
+        sptrsv_transform_params_t q = *prm;
+        q.select_mode = mode;
+        q.depth = depth;
+        if (mode == SPTRSV_SELECT_HEURISTIC) {
+            q.thin_rows = thin;
+            q.max_depth = dmax;
+            q.flop_budget = rho;
+        }
+        cands.push_back({code, q});
+    };
+    add(0, SPTRSV_SELECT_NONE, 0, 0, 0, 0);
+    for (int d = 1; d <= 3; ++d) add(d, SPTRSV_SELECT_FIXED, d, 0, 0, 0);
+    add(200, SPTRSV_SELECT_HEURISTIC, 0, prm->thin_rows, prm->max_depth, prm->flop_budget);
+    add(kThinOnly + 8, SPTRSV_SELECT_HEURISTIC, 0, kThinRows, 8, kThinBudget);
+    add(kThinOnly + 16, SPTRSV_SELECT_HEURISTIC, 0, kThinRows, 16, kThinBudget);
+    if (p->costmodel || default_costmodel()) {
+        sptrsv_transform_params_t q = *prm;
+        q.select_mode = SPTRSV_SELECT_COSTMODEL;
+        q.solve_mode = SPTRSV_SOLVE_SYNCFREE;
+        q.lanes_per_row = 1;
+        CKS(sptrsv_transform(p, &q, stream));
+        const int code = p->chosen_depth;
+        if (code >= 0 && code < kThinOnly)
+            add(code, SPTRSV_SELECT_FIXED, code, 0, 0, 0);
+        else if (code >= kThinOnly)
+            add(code, SPTRSV_SELECT_HEURISTIC, 0, kThinRows, code - kThinOnly, kThinBudget);
+    }
+    DevArr<double> b, x;
+    CK(b.alloc(std::max<int32_t>(p->n, 1)));
+    CK(x.alloc(std::max<int32_t>(p->n, 1)));
+    std::vector<double> ones(std::max<int32_t>(p->n, 1), 1.0);
+    CK(cudaMemcpyAsync(b.p, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice,
+                       s));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best_ms = 1e30;
+    int best = 0;
+    sptrsv_status_t st = SPTRSV_OK;
+    for (size_t i = 0; i < cands.size() && st == SPTRSV_OK; ++i) {
+        for (int L : {1, 4}) {
+            sptrsv_transform_params_t q = cands[i].q;
+            q.solve_mode = SPTRSV_SOLVE_SYNCFREE;
+            q.lanes_per_row = L;
+            q.block_threads = 256;
+            q.grid_blocks = 0;
+            q.tail_rows = -1;
+            if ((st = sptrsv_transform(p, &q, stream)) != SPTRSV_OK) break;
+            double ms = 1e30;
+            for (int r = 0; r < 4 && st == SPTRSV_OK; ++r) {
+                if (cudaEventRecord(e0, s) != cudaSuccess) st = SPTRSV_ERR_CUDA;
+                if (st == SPTRSV_OK) st = solve_impl(p, b.p, x.p, 1, s);
+                if (st == SPTRSV_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
+                                        cudaEventSynchronize(e1) != cudaSuccess))
+                    st = SPTRSV_ERR_CUDA;
+                float t = 0;
+                if (st == SPTRSV_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+                    st = SPTRSV_ERR_CUDA;
+                if (r > 0) ms = std::min(ms, (double)t);   // the first is the warm-up
+            }
+            if (st == SPTRSV_OK) st = sync_status(p, s);
+            if (st == SPTRSV_OK && ms < best_ms) {
+                best_ms = ms;
+                best = (int)i;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SPTRSV_OK) return st;
+    CKS(sptrsv_transform(p, &cands[best].q, stream));
+    p->chosen_depth = cands[best].code;
+    p->prm.select_mode = SPTRSV_SELECT_AUTO;
+    p->transform_ms = now_ms() - t0;
+    return SPTRSV_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1372,6 +1467,7 @@ sptrsv_status_t sptrsv_transform(sptrsv_plan_t p, const sptrsv_transform_params_
                                  sptrsv_stream_t stream) {
     if (!p || !prm) return SPTRSV_ERR_INVALID_ARG;
     if (p->latched != SPTRSV_OK) return SPTRSV_ERR_BAD_STATE;
+    if (prm->select_mode == SPTRSV_SELECT_AUTO) return select_auto(p, prm, stream);
     if (prm->select_mode < 0 || prm->select_mode > 3 || prm->solve_mode < 0 ||
         prm->solve_mode > 2 || (prm->precision != SPTRSV_F64 && prm->precision != SPTRSV_F32_IR))
         return SPTRSV_ERR_INVALID_ARG;

@@ -7,7 +7,9 @@
 // Parameter layout (one flat FP32 array): W1[F][H], b1[H], W2[H][H], b2[H],
 // W3[H][1], b3[1]; row-major, X is [N][F].
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "plan.cuh"
@@ -128,6 +130,42 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g,
 
 unsigned blocks(int64_t n, int bs = 256) { return (unsigned)((n + bs - 1) / bs); }
 
+// Column statistics of X [N][F]: one block per feature, FP64 sums in a fixed
+// order (per-thread strided partial sums, then thread 0 adds them in order).
+__global__ void column_stats_kernel(const float *__restrict__ X, int N, int F,
+                                    double *__restrict__ mean, double *__restrict__ var) {
+    __shared__ double ps[256], pq[256];
+    const int f = blockIdx.x;
+    double s = 0.0, q = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double v = X[(int64_t)i * F + f];
+        s += v;
+        q = fma(v, v, q);
+    }
+    ps[threadIdx.x] = s;
+    pq[threadIdx.x] = q;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ts = 0.0, tq = 0.0;
+        for (int k = 0; k < (int)blockDim.x; ++k) {
+            ts += ps[k];
+            tq += pq[k];
+        }
+        const double m = ts / N;
+        mean[f] = m;
+        var[f] = fmax(tq / N - m * m, 0.0);
+    }
+}
+
+__global__ void normalize_kernel(const float *__restrict__ X, float *__restrict__ Xn, int64_t n,
+                                 int F, const float *__restrict__ mean,
+                                 const float *__restrict__ inv_std) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int f = (int)(t % F);
+    Xn[t] = (X[t] - mean[f]) * inv_std[f];
+}
+
 sptrsv_status_t ensure_cap(sptrsv_mlp_t net, int64_t N) {
     if (N <= net->cap) return SPTRSV_OK;
     const int64_t H = net->H;
@@ -203,7 +241,21 @@ sptrsv_status_t costmodel_predict(sptrsv_mlp_t net, const float *h_feat, int cou
         return SPTRSV_ERR_CUDA;
     return SPTRSV_OK;
 }
+// The process-wide default network of SELECT_COSTMODEL (sptrsv_costmodel_load).
+std::mutex g_default_mu;
+sptrsv_mlp_t g_default_net = nullptr;
+sptrsv_mlp_t default_costmodel() {
+    std::lock_guard<std::mutex> lock(g_default_mu);
+    return g_default_net;
+}
 }  // namespace sptrsv
+
+namespace {
+// Network file (little-endian): 8 bytes "SPTRSVNN", int32 version (1), F, H,
+// has_norm; float32 params[nparams(F, H)], mean[F], std[F].
+constexpr char kNetMagic[8] = {'S', 'P', 'T', 'R', 'S', 'V', 'N', 'N'};
+constexpr int32_t kNetVersion = 1;
+}  // namespace
 
 extern "C" {
 
@@ -299,8 +351,142 @@ SPTRSV_API sptrsv_status_t sptrsv_mlp_train_step(sptrsv_mlp_t net, const float *
 
 SPTRSV_API void sptrsv_mlp_destroy(sptrsv_mlp_t net) {
     if (!net) return;
+    {
+        std::lock_guard<std::mutex> lock(sptrsv::g_default_mu);
+        if (sptrsv::g_default_net == net) sptrsv::g_default_net = nullptr;
+    }
     cudaDeviceSynchronize();
     delete net;
+}
+
+SPTRSV_API sptrsv_status_t sptrsv_mlp_fit_normalization(sptrsv_mlp_t net, const float *d_X,
+                                                        int32_t N, sptrsv_stream_t stream) {
+    if (!net || N < 1 || !d_X) return SPTRSV_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int F = net->F;
+    DevArr<double> mv;
+    if (mv.alloc(2 * (size_t)F)) return SPTRSV_ERR_OOM;
+    column_stats_kernel<<<F, 256, 0, s>>>(d_X, N, F, mv.p, mv.p + F);
+    std::vector<double> h(2 * (size_t)F);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(h.data(), mv.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s) ||
+        cudaStreamSynchronize(s))
+        return SPTRSV_ERR_CUDA;
+    for (int f = 0; f < F; ++f) {
+        const double sd = std::sqrt(h[F + f]);
+        net->feat_mean[f] = (float)h[f];
+        net->feat_std[f] = sd > 1e-6 ? (float)sd : 1.f;
+    }
+    net->has_norm = true;
+    return SPTRSV_OK;
+}
+
+SPTRSV_API sptrsv_status_t sptrsv_mlp_get_normalization(sptrsv_mlp_t net, float *h_mean,
+                                                        float *h_std) {
+    if (!net || !h_mean || !h_std) return SPTRSV_ERR_INVALID_ARG;
+    for (int f = 0; f < net->F; ++f) {
+        h_mean[f] = net->has_norm ? net->feat_mean[f] : 0.f;
+        h_std[f] = net->has_norm ? net->feat_std[f] : 1.f;
+    }
+    return SPTRSV_OK;
+}
+
+SPTRSV_API sptrsv_status_t sptrsv_mlp_normalize(sptrsv_mlp_t net, const float *d_X, int32_t N,
+                                                float *d_Xn, sptrsv_stream_t stream) {
+    if (!net || N < 0 || (N > 0 && (!d_X || !d_Xn))) return SPTRSV_ERR_INVALID_ARG;
+    if (N == 0) return SPTRSV_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int F = net->F;
+    std::vector<float> h(2 * (size_t)F);
+    for (int f = 0; f < F; ++f) {
+        h[f] = net->has_norm ? net->feat_mean[f] : 0.f;
+        h[F + f] = net->has_norm ? 1.f / net->feat_std[f] : 1.f;
+    }
+    DevArr<float> st;
+    if (st.alloc(h.size())) return SPTRSV_ERR_OOM;
+    const int64_t n = (int64_t)N * F;
+    if (cudaMemcpyAsync(st.p, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, s))
+        return SPTRSV_ERR_CUDA;
+    normalize_kernel<<<blocks(n), 256, 0, s>>>(d_X, d_Xn, n, F, st.p, st.p + F);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s)) return SPTRSV_ERR_CUDA;
+    return SPTRSV_OK;
+}
+
+SPTRSV_API sptrsv_status_t sptrsv_mlp_save(sptrsv_mlp_t net, const char *path) {
+    if (!net || !path) return SPTRSV_ERR_INVALID_ARG;
+    std::vector<float> params(net->nparams);
+    if (cudaMemcpy(params.data(), net->params.p, net->nparams * sizeof(float),
+                   cudaMemcpyDeviceToHost))
+        return SPTRSV_ERR_CUDA;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return SPTRSV_ERR_INVALID_ARG;
+    const int32_t hdr[4] = {kNetVersion, net->F, net->H, net->has_norm ? 1 : 0};
+    bool ok = std::fwrite(kNetMagic, 1, 8, f) == 8 && std::fwrite(hdr, 4, 4, f) == 4 &&
+              std::fwrite(params.data(), 4, params.size(), f) == params.size() &&
+              std::fwrite(net->feat_mean, 4, net->F, f) == (size_t)net->F &&
+              std::fwrite(net->feat_std, 4, net->F, f) == (size_t)net->F;
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? SPTRSV_OK : SPTRSV_ERR_INVALID_ARG;
+}
+
+SPTRSV_API sptrsv_status_t sptrsv_mlp_load(const char *path, sptrsv_mlp_t *out) {
+    if (!path || !out) return SPTRSV_ERR_INVALID_ARG;
+    *out = nullptr;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return SPTRSV_ERR_INVALID_ARG;
+    char magic[8];
+    int32_t hdr[4];
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kNetMagic, 8) == 0 &&
+              std::fread(hdr, 4, 4, f) == 4 && hdr[0] == kNetVersion && hdr[1] >= 1 &&
+              hdr[1] <= 64 && hdr[2] >= 1 && hdr[2] <= 1024;
+    std::vector<float> params, mean, sd;
+    if (ok) {
+        params.resize(offsets(hdr[1], hdr[2]).total);
+        mean.resize(hdr[1]);
+        sd.resize(hdr[1]);
+        ok = std::fread(params.data(), 4, params.size(), f) == params.size() &&
+             std::fread(mean.data(), 4, mean.size(), f) == mean.size() &&
+             std::fread(sd.data(), 4, sd.size(), f) == sd.size();
+        char extra;
+        ok = ok && std::fread(&extra, 1, 1, f) == 0;   // nothing after the weights
+    }
+    std::fclose(f);
+    if (!ok) return SPTRSV_ERR_INVALID_ARG;
+    sptrsv_mlp_t net = nullptr;
+    sptrsv_status_t st = sptrsv_mlp_create(hdr[1], hdr[2], params.data(), &net);
+    if (st != SPTRSV_OK) return st;
+    if (hdr[3]) sptrsv_mlp_set_normalization(net, mean.data(), sd.data());
+    *out = net;
+    return SPTRSV_OK;
+}
+
+SPTRSV_API sptrsv_status_t sptrsv_costmodel_load(const char *path) {
+    sptrsv_mlp_t net = nullptr;
+    sptrsv_status_t st = sptrsv_mlp_load(path, &net);
+    if (st != SPTRSV_OK) return st;
+    sptrsv_mlp_t old;
+    {
+        std::lock_guard<std::mutex> lock(sptrsv::g_default_mu);
+        old = sptrsv::g_default_net;
+        sptrsv::g_default_net = net;
+    }
+    if (old) {
+        cudaDeviceSynchronize();
+        delete old;
+    }
+    return SPTRSV_OK;
+}
+
+SPTRSV_API sptrsv_status_t sptrsv_costmodel_save(const char *path) {
+    std::lock_guard<std::mutex> lock(sptrsv::g_default_mu);
+    if (!sptrsv::g_default_net) return SPTRSV_ERR_BAD_STATE;
+    return sptrsv_mlp_save(sptrsv::g_default_net, path);
+}
+
+SPTRSV_API sptrsv_status_t sptrsv_costmodel_set_default(sptrsv_mlp_t net) {
+    std::lock_guard<std::mutex> lock(sptrsv::g_default_mu);
+    sptrsv::g_default_net = net;
+    return SPTRSV_OK;
 }
 
 }  // extern "C"

@@ -123,3 +123,24 @@ def test_pcg_host_side_argument_errors(lib):
     assert lib.sptrsv_pcg_get_factor(None, ctypes.byref(nnz), None, None) == 1
     lib.sptrsv_pcg_destroy(None)
     assert (B.PRECOND_SGS, B.PRECOND_IC0) == (0, 1)
+
+
+def test_network_files_are_checked_before_any_device_work(tmp_path, lib):
+    """Missing, foreign and short network files are refused with
+    SPTRSV_ERR_INVALID_ARG, and saving the process-wide model when none is
+    loaded with SPTRSV_ERR_BAD_STATE -- all before any device call."""
+    from paper_2103_11445_gb300 import binding as B
+    missing = str(tmp_path / "missing.bin")
+    foreign = tmp_path / "foreign.bin"
+    foreign.write_bytes(b"NOTANET!" + bytes(64))
+    short = tmp_path / "short.bin"
+    import struct
+    short.write_bytes(b"SPTRSVNN" + struct.pack("<4i", 1, 17, 64, 1) + bytes(40))
+    for path in (missing, str(foreign), str(short)):
+        out = ctypes.c_void_p()
+        assert lib.sptrsv_mlp_load(os.fsencode(path), ctypes.byref(out)) == 1
+        assert not out.value
+        assert lib.sptrsv_costmodel_load(os.fsencode(path)) == 1
+    assert lib.sptrsv_costmodel_save(os.fsencode(str(tmp_path / "x.bin"))) == 9
+    with pytest.raises(B.SptrsvError):
+        B.sptrsv_costmodel_save(str(tmp_path / "y.bin"))

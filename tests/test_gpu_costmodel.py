@@ -10,6 +10,7 @@ import matgen as mg
 import oracle
 from oracle import mlp as omlp
 from oracle import rewrite as rw
+from gpu_util import assert_close_to_oracle, gpu_solve, plan_for
 
 pytestmark = pytest.mark.gpu
 
@@ -174,3 +175,52 @@ def test_costmodel_fallback_is_the_heuristic():
     P.transform(select_mode=B.SELECT_HEURISTIC, solve_mode=B.SOLVE_BARRIER)
     assert P.segments() == seg_cm
     P.close()
+
+
+def test_network_file_round_trip_and_default_model(tmp_path):
+    """sptrsv_mlp_save / sptrsv_mlp_load and the process-wide model of
+    sptrsv_costmodel_load / _save, through the C ABI: the loaded network has
+    the same weights and normalisation, predicts the same values, and
+    SELECT_COSTMODEL without an attached network picks the same candidate
+    as with the original attached."""
+    import torch
+    from paper_2103_11445_gb300 import binding as B
+    from paper_2103_11445_gb300.costmodel import CostModel, N_FEATURES
+    rng = np.random.default_rng(5)
+    X = rng.normal(size=(64, N_FEATURES)).astype(np.float32) * 3 + 1
+    y = rng.normal(size=64).astype(np.float32)
+    m = CostModel(seed=3)
+    m.fit(X, y, epochs=20)
+    f1 = str(tmp_path / "net.bin")
+    m.save(f1)
+    q = CostModel.load(f1)
+    assert np.array_equal(q.params(), m.params())
+    assert np.array_equal(q.mean, m.mean) and np.array_equal(q.std, m.std)
+    assert np.array_equal(q.predict(X), m.predict(X))
+    # the statistics are the library's: column means and deviations of X
+    assert np.allclose(m.mean, X.mean(axis=0), rtol=1e-5, atol=1e-5)
+    assert np.allclose(m.std, X.std(axis=0), rtol=1e-4)
+    # the process-wide model
+    A = mg.stencil3d(24, seed=8)
+    P = plan_for(A)
+    m.attach(P)
+    P.transform(select_mode=2, solve_mode=2)
+    pick = P.info()["chosen_depth"]
+    B.sptrsv_costmodel_load(f1)
+    f2 = str(tmp_path / "default.bin")
+    B.sptrsv_costmodel_save(f2)
+    assert open(f1, "rb").read() == open(f2, "rb").read()
+    Q = plan_for(A)
+    Q.transform(select_mode=2, solve_mode=2)
+    assert Q.info()["chosen_depth"] == pick
+    b = mg.rhs_uniform(A.n, seed=1)
+    assert_close_to_oracle(A, gpu_solve(Q, b), b, 1e-10)
+    B.sptrsv_costmodel_set_default(0)
+    Q.transform(select_mode=2, solve_mode=2)
+    assert Q.info()["chosen_depth"] == -1        # no network: heuristic H
+    with pytest.raises(B.SptrsvError):
+        B.sptrsv_costmodel_save(str(tmp_path / "none.bin"))
+    for c in (m, q):
+        c.close()
+    P.close()
+    Q.close()

@@ -199,3 +199,27 @@ def test_autotune_cache_reuses_the_launch_for_the_same_shape():
     B.sptrsv_autotune_cache_clear()
     P.transform(select_mode=3, depth=2)
     assert P.info()["tuned_from_cache"] == 0
+
+
+def test_select_auto_keeps_a_timed_candidate():
+    """SELECT_AUTO times its candidates inside sptrsv_transform and keeps one
+    of them: the plan's segments are those of the candidate it names, and
+    the solve matches the oracle."""
+    A = mg.stencil3d(24, seed=8)
+    P = plan_for(A, select_mode=4, solve_mode=2)
+    info = P.info()
+    assert info["select_mode"] == 4
+    code = info["chosen_depth"]
+    assert code in (0, 1, 2, 3, 200, 108, 116)
+    if code == 0:
+        kw = dict(select_mode=0)
+    elif code == 200:
+        kw = dict(select_mode=1)
+    elif code >= 100:
+        kw = dict(select_mode=1, thin_rows=32, max_depth=code - 100, flop_budget=4.0)
+    else:
+        kw = dict(select_mode=3, depth=code)
+    Q = plan_for(A, solve_mode=2, **kw)
+    assert P.segments() == Q.segments()
+    b = mg.rhs_uniform(A.n, seed=9)
+    assert_close_to_oracle(A, gpu_solve(P, b), b, TOL64)
