@@ -22,7 +22,11 @@ Contents (each function cites the passage of the paper it follows):
   network -- numpy, ``mlp.py``;
 * ``pcg``            preconditioned conjugate gradients with the symmetric
   Gauss-Seidel preconditioner (two triangular solves per step) -- numpy and
-  the substitutions above, ``pcg.py``.
+  the substitutions above, ``pcg.py``;
+* ``critpath``       weighted critical path of a (transformed) system and
+  the critical-path-driven segment selection for synchronisation-free
+  solves (Sec. III's remark that rewriting applies to them) -- Python,
+  ``critpath.py``.
 
 Parity status: every function above is pinned by tests against closed
 forms, exact rational arithmetic, library routines or brute force; the
