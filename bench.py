@@ -318,6 +318,8 @@ def code_kw(code: int, Bd) -> dict:
         return dict(select_mode=Bd.SELECT_NONE)
     if code == 200:
         return dict(select_mode=Bd.SELECT_HEURISTIC)
+    if code == 300:
+        return dict(select_mode=Bd.SELECT_CRITPATH, max_depth=4)
     if code >= 100:
         return dict(select_mode=Bd.SELECT_HEURISTIC, thin_rows=32, max_depth=code - 100,
                     flop_budget=4.0)
@@ -329,6 +331,8 @@ def code_name(code: int) -> str:
         return "plain"
     if code == 200:
         return "heuristic"
+    if code == 300:
+        return "critpath_d4"
     if code >= 100:
         return f"heuristic_thin32_d{code - 100}"
     return f"fixed_d{code}"
@@ -438,7 +442,8 @@ def run_ours(args, world, rank, local):
     # transformed the same way and reported beside it, not searched over.
     cands = [("library_auto", dict(select_mode=Bd.SELECT_AUTO)),
              ("plain", dict(select_mode=Bd.SELECT_NONE)),
-             ("heuristic", dict(select_mode=Bd.SELECT_HEURISTIC))]
+             ("heuristic", dict(select_mode=Bd.SELECT_HEURISTIC)),
+             ("critpath_d4", dict(select_mode=Bd.SELECT_CRITPATH, max_depth=4))]
     for d in [int(v) for v in args.depths.split(",") if v.strip()]:
         cands.append((f"fixed_d{d}", dict(select_mode=Bd.SELECT_FIXED, depth=d)))
     results = {}

@@ -82,14 +82,29 @@ enum {
                                      (sptrsv_set_costmodel or
                                      sptrsv_costmodel_load; else H) */
     SPTRSV_SELECT_FIXED = 3,      /* merge every `depth`+1 consecutive levels */
-    SPTRSV_SELECT_AUTO = 4        /* measured: times the candidates below on
+    SPTRSV_SELECT_AUTO = 4,       /* measured: times the candidates below on
                                      the plan and keeps the fastest */
+    SPTRSV_SELECT_CRITPATH = 5    /* minimises the critical path of the
+                                     synchronisation-free solve (below) */
 };
+/* SPTRSV_SELECT_CRITPATH (the rewriting applied to synchronisation-free
+ * execution, Sec. III): a row finishes one hop after the latest of its
+ * dependencies plus its own terms, f(i) = hop_weight + terms(i) + max f(dep).
+ * If every row of a new level waits for the whole level before it, the
+ * plan's critical path is the sum over new levels of hop_weight + (most
+ * terms of a row in it) -- an upper bound of the weighted critical path of
+ * the transformed system.  The segmentation minimising that sum is found by
+ * dynamic programming over the levels (last level first, ties to the
+ * smaller depth), each segment absorbing at most max_depth levels with no
+ * rewritten row above max_row_fill terms; every lift (level l rewritten to
+ * l - r, r <= max_depth) is counted on the device first, so the cost grows
+ * with max_depth. */
 /* SPTRSV_SELECT_AUTO: the candidates are the plain level sets (code 0),
  * merging every d+1 levels for d = 1, 2, 3 (code d), heuristic H with the
  * given thin_rows / max_depth / flop_budget (code 200), H on the levels of
  * fewer than 32 rows, up to 8 or 16 deep, within 4x the plain FLOPs (codes
- * 108, 116), and the cost model's pick when a network is available (its
+ * 108, 116), the critical-path selection with at most 4 levels per segment
+ * (code 300), and the cost model's pick when a network is available (its
  * code).  Each is built and timed with the synchronisation-free kernel at 1
  * and at 4 lanes per row (one warm-up and three solves of a vector of ones,
  * the fastest counts); the fastest candidate is then transformed with the
@@ -164,6 +179,8 @@ typedef struct {
                                 capped so that the slots of every resident
                                 warp fit an SM's shared memory), < 0 = off,
                                 > 12 = 12. */
+    int32_t hop_weight;      /* SELECT_CRITPATH: weight of one dependency hop
+                                in units of one term of a row (<= 0: 16) */
 } sptrsv_transform_params_t;
 
 /* Everything a caller may want to report about a plan. */
@@ -535,6 +552,15 @@ SPTRSV_API sptrsv_status_t sptrsv_last_kernel_ms(sptrsv_plan_t p, float *ms);
  * sptrsv_transform rebuilds the structure from the matrix, which removes
  * the injected dependency. */
 SPTRSV_API sptrsv_status_t sptrsv_debug_inject_wait(sptrsv_plan_t p, int32_t row);
+
+/* Weighted critical path of the plan's current FP64 solve structure (the
+ * system the solve kernels run, rewritten rows included): CP = max over rows
+ * of f(i) = hop_weight + terms(i) + max f(j) over the unknowns j its x terms
+ * read, terms(i) = its x terms plus b terms (hop_weight <= 0: 16).  Computed
+ * on the device one new level per launch; synchronises `stream`.
+ * SPTRSV_ERR_BAD_STATE before the structure exists. */
+SPTRSV_API sptrsv_status_t sptrsv_critical_path(sptrsv_plan_t p, int32_t hop_weight,
+                                                int64_t *h_cp, sptrsv_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -24,7 +24,8 @@ STATUS_NAMES = {
     5: "MISSING_DIAG", 6: "OOM", 7: "CUDA", 8: "TIMEOUT", 9: "BAD_STATE",
     10: "UNSUPPORTED", 11: "BREAKDOWN",
 }
-SELECT_NONE, SELECT_HEURISTIC, SELECT_COSTMODEL, SELECT_FIXED, SELECT_AUTO = 0, 1, 2, 3, 4
+SELECT_NONE, SELECT_HEURISTIC, SELECT_COSTMODEL, SELECT_FIXED, SELECT_AUTO, SELECT_CRITPATH = \
+    0, 1, 2, 3, 4, 5
 SOLVE_AUTO, SOLVE_BARRIER, SOLVE_SYNCFREE = 0, 1, 2
 F64, F32_IR = 0, 1
 OP_LOWER, OP_UPPER, OP_LOWER_TRANS, OP_UPPER_TRANS = 0, 1, 2, 3
@@ -47,7 +48,7 @@ class TransformParams(Structure):
         ("lanes_per_row", c_int32), ("block_threads", c_int32),
         ("cta_run_rows", c_int32), ("wait_timeout_ms", c_int32),
         ("grid_blocks", c_int32), ("poll_backoff_ns", c_int32), ("nrhs_hint", c_int32),
-        ("tail_rows", c_int32), ("stage_z", c_int32),
+        ("tail_rows", c_int32), ("stage_z", c_int32), ("hop_weight", c_int32),
     ]
 
 
@@ -94,6 +95,7 @@ _SIGS = {
                                          c_void_p, c_void_p, c_void_p, c_void_p,
                                          c_void_p]),
     "sptrsv_debug_inject_wait": (c_int32, [c_void_p, c_int32]),
+    "sptrsv_critical_path": (c_int32, [c_void_p, c_int32, POINTER(c_int64), c_void_p]),
     "sptrsv_costmodel_features": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "sptrsv_set_costmodel": (c_int32, [c_void_p, c_void_p]),
     "sptrsv_mlp_num_params": (c_int64, [c_int32, c_int32]),
@@ -244,6 +246,13 @@ def sptrsv_get_transformed(plan: int, d_new_level: int, d_xptr: int, d_xcol: int
 
 def sptrsv_debug_inject_wait(plan: int, row: int) -> None:
     _check(load().sptrsv_debug_inject_wait(plan, row), "sptrsv_debug_inject_wait")
+
+
+def sptrsv_critical_path(plan: int, hop_weight: int = 0, stream: int = 0) -> int:
+    cp = c_int64()
+    _check(load().sptrsv_critical_path(plan, hop_weight, byref(cp), stream),
+           "sptrsv_critical_path")
+    return cp.value
 
 
 def sptrsv_solve_ir_noalloc(plan: int, d_b: int, d_x: int, nrhs: int,

@@ -112,6 +112,7 @@ struct FillQuery {
     cudaStream_t s;
     int cap;
     std::map<std::pair<int32_t, int32_t>, int64_t> cache;  // -1: overflow
+    std::map<std::pair<int32_t, int32_t>, int32_t> maxlen;  // most terms of a lifted row
     sptrsv_status_t err = SPTRSV_OK;
 
     sptrsv_status_t run(const std::vector<std::pair<int32_t, int32_t>> &qs_in) {
@@ -128,7 +129,7 @@ struct FillQuery {
         const int32_t nq = (int32_t)ql.size();
         if (nq == 0) return SPTRSV_OK;
         const int64_t nitems = qoff.back();
-        DevArr<int32_t> d_ql, d_qt, irow, itgt, iq, ovf;
+        DevArr<int32_t> d_ql, d_qt, irow, itgt, iq, ovf, mlen;
         DevArr<int64_t> d_qoff;
         DevArr<unsigned long long> added;
         CK(upload(d_ql, ql, s));
@@ -138,21 +139,28 @@ struct FillQuery {
         CK(itgt.alloc(nitems));
         CK(iq.alloc(nitems));
         CK(ovf.alloc(nq));
+        CK(mlen.alloc(nq));
         CK(added.alloc(nq));
         CK(cudaMemsetAsync(ovf.p, 0, nq * sizeof(int32_t), s));
+        CK(cudaMemsetAsync(mlen.p, 0, nq * sizeof(int32_t), s));
         CK(cudaMemsetAsync(added.p, 0, nq * sizeof(unsigned long long), s));
         CK(launch_expand_queries(nq, d_ql.p, d_qt.p, d_qoff.p, p->level_ptr.p, p->perm.p, irow.p,
                                  itgt.p, iq.p, nullptr, s));
         CK(launch_rewrite_count(nitems, irow.p, itgt.p, iq.p, p->row_ptr.p, p->col.p,
-                                p->level.p, cap, nullptr, added.p, ovf.p, p->num_sms, s));
-        std::vector<int32_t> h_ovf(nq);
+                                p->level.p, cap, nullptr, added.p, ovf.p, mlen.p, p->num_sms,
+                                s));
+        std::vector<int32_t> h_ovf(nq), h_mlen(nq);
         std::vector<unsigned long long> h_add(nq);
         CK(cudaMemcpyAsync(h_ovf.data(), ovf.p, nq * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(h_add.data(), added.p, nq * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h_mlen.data(), mlen.p, nq * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           s));
         CK(cudaStreamSynchronize(s));
-        for (int32_t i = 0; i < nq; ++i)
+        for (int32_t i = 0; i < nq; ++i) {
             cache[{ql[i], ql[i] - qt[i]}] = h_ovf[i] ? -1 : (int64_t)h_add[i];
+            maxlen[{ql[i], ql[i] - qt[i]}] = h_mlen[i];
+        }
         return SPTRSV_OK;
     }
 
@@ -209,6 +217,49 @@ sptrsv_status_t compute_segments(sptrsv_plan_t p, int64_t tau, int32_t d_max, do
     for (auto &sg : *out)
         for (int32_t r = 1; r <= sg.second; ++r) tot += fo.cache[{sg.first + r, r}];
     *added_flops = tot;
+    return SPTRSV_OK;
+}
+
+// SELECT_CRITPATH: the segmentation minimising the level-set critical path
+// sum over new levels of (hop + most terms of a row in it), by dynamic
+// programming over the levels, last first, ties to the smaller depth; every
+// lift (l, r <= d_max) is counted on the device first.
+sptrsv_status_t critpath_segments(sptrsv_plan_t p, int64_t hop, int32_t d_max, cudaStream_t s,
+                                  std::vector<std::pair<int32_t, int32_t>> *out) {
+    const int32_t nlev = p->nlev;
+    std::vector<int32_t> lm0(nlev, 0);
+    {
+        DevArr<int32_t> lm;
+        CK(lm.alloc(nlev));
+        CK(cudaMemsetAsync(lm.p, 0, nlev * sizeof(int32_t), s));
+        CK(launch_level_max(p->n, p->level.p, p->offdeg.p, lm.p, s));
+        CK(cudaMemcpyAsync(lm0.data(), lm.p, nlev * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    FillQuery fo{p, s, p->prm.max_row_fill, {}};
+    std::vector<std::pair<int32_t, int32_t>> qs;
+    for (int32_t l = 1; l < nlev; ++l)
+        for (int32_t r = 1; r <= std::min(d_max, l); ++r) qs.emplace_back(l, r);
+    CKS(fo.run(qs));
+    std::vector<double> best(nlev + 1, INFINITY);
+    std::vector<int32_t> choice(nlev + 1, 0);
+    best[nlev] = 0.0;
+    for (int32_t t = nlev - 1; t >= 0; --t) {
+        int64_t m = lm0[t];
+        for (int32_t d = 0; d <= d_max && t + d < nlev; ++d) {
+            if (d > 0) {
+                if (fo.cache[{t + d, d}] < 0) break;   // a row would exceed the fill cap
+                m = std::max<int64_t>(m, fo.maxlen[{t + d, d}]);
+            }
+            const double c = (double)(hop + m) + best[t + d + 1];
+            if (c < best[t]) {
+                best[t] = c;
+                choice[t] = d;
+            }
+        }
+    }
+    out->clear();
+    for (int32_t t = 0; t < nlev; t += choice[t] + 1) out->emplace_back(t, choice[t]);
     return SPTRSV_OK;
 }
 
@@ -310,6 +361,15 @@ sptrsv_status_t choose_segments(sptrsv_plan_t p, cudaStream_t s) {
             d_max = kCostDepths[best];
             rho = INFINITY;
         }
+    } else if (prm.select_mode == SPTRSV_SELECT_CRITPATH) {
+        std::vector<std::pair<int32_t, int32_t>> segs;
+        CKS(critpath_segments(p, prm.hop_weight > 0 ? prm.hop_weight : 16, prm.max_depth, s,
+                              &segs));
+        for (auto &sg : segs) {
+            p->seg_first.push_back(sg.first);
+            p->seg_depth.push_back(sg.second);
+        }
+        return SPTRSV_OK;
     } else if (prm.select_mode == SPTRSV_SELECT_FIXED) {
         tau = INT64_MAX;
         d_max = prm.depth;
@@ -372,7 +432,7 @@ sptrsv_status_t build_rewritten(sptrsv_plan_t p, cudaStream_t s) {
                              itgt.p, nullptr, ipos.p, s));
     const int cap = p->prm.max_row_fill;
     CK(launch_rewrite_count(nitems, irow.p, itgt.p, nullptr, p->row_ptr.p, p->col.p, p->level.p,
-                            cap, fill.p, nullptr, nullptr, p->num_sms, s));
+                            cap, fill.p, nullptr, nullptr, nullptr, p->num_sms, s));
     CK(p->rw_off.alloc(nitems + 1));
     CK(stmp.alloc(scan_tmp_elems(nitems)));
     CK(exclusive_scan_i32_i64(fill.p, p->rw_off.p, nitems, stmp.p, s));
@@ -1179,6 +1239,12 @@ sptrsv_status_t select_auto(sptrsv_plan_t p, const sptrsv_transform_params_t *pr
     add(200, SPTRSV_SELECT_HEURISTIC, 0, prm->thin_rows, prm->max_depth, prm->flop_budget);
     add(kThinOnly + 8, SPTRSV_SELECT_HEURISTIC, 0, kThinRows, 8, kThinBudget);
     add(kThinOnly + 16, SPTRSV_SELECT_HEURISTIC, 0, kThinRows, 16, kThinBudget);
+    {   // the critical-path selection, at most 4 levels per segment
+        sptrsv_transform_params_t q = *prm;
+        q.select_mode = SPTRSV_SELECT_CRITPATH;
+        q.max_depth = std::min(std::max(prm->max_depth, 1), 4);
+        cands.push_back({300, q});
+    }
     if (p->costmodel || default_costmodel()) {
         sptrsv_transform_params_t q = *prm;
         q.select_mode = SPTRSV_SELECT_COSTMODEL;
@@ -1468,7 +1534,7 @@ sptrsv_status_t sptrsv_transform(sptrsv_plan_t p, const sptrsv_transform_params_
     if (!p || !prm) return SPTRSV_ERR_INVALID_ARG;
     if (p->latched != SPTRSV_OK) return SPTRSV_ERR_BAD_STATE;
     if (prm->select_mode == SPTRSV_SELECT_AUTO) return select_auto(p, prm, stream);
-    if (prm->select_mode < 0 || prm->select_mode > 3 || prm->solve_mode < 0 ||
+    if (prm->select_mode < 0 || prm->select_mode > 5 || prm->solve_mode < 0 ||
         prm->solve_mode > 2 || (prm->precision != SPTRSV_F64 && prm->precision != SPTRSV_F32_IR))
         return SPTRSV_ERR_INVALID_ARG;
     if (prm->lanes_per_row != 0 && prm->lanes_per_row != 1 && prm->lanes_per_row != 2 &&
@@ -1690,6 +1756,30 @@ sptrsv_status_t sptrsv_last_kernel_ms(sptrsv_plan_t p, float *ms) {
     if (!p->prof_valid) return SPTRSV_ERR_BAD_STATE;
     CK(cudaEventSynchronize(p->prof_ev[1]));
     CK(cudaEventElapsedTime(ms, p->prof_ev[0], p->prof_ev[1]));
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_critical_path(sptrsv_plan_t p, int32_t hop_weight, int64_t *h_cp,
+                                     sptrsv_stream_t stream) {
+    if (!p || !h_cp) return SPTRSV_ERR_INVALID_ARG;
+    if (p->latched != SPTRSV_OK) return SPTRSV_ERR_BAD_STATE;
+    *h_cp = 0;
+    if (p->n == 0) return SPTRSV_OK;
+    const SolveStruct<double> &ss = p->s64;
+    if (!ss.built) return SPTRSV_ERR_BAD_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t hop = hop_weight > 0 ? hop_weight : 16;
+    DevArr<int64_t> fin;
+    CK(fin.alloc(p->n));
+    CK(cudaMemsetAsync(fin.p, 0, (size_t)p->n * sizeof(int64_t), s));
+    const int32_t *p0 = ss.run_encoded > 0 ? ss.chunk_run_p0.p : nullptr;
+    for (int32_t l = 0; l < ss.nlev; ++l)
+        CK(launch_critpath_level(ss.h_lvl_chunk[l], ss.h_lvl_chunk[l + 1], ss.L, p->n,
+                                 ss.meta.p, ss.ecol.p, ss.row_id.p, p0, hop, fin.p, s));
+    std::vector<int64_t> h(p->n);
+    CK(cudaMemcpyAsync(h.data(), fin.p, h.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *h_cp = *std::max_element(h.begin(), h.end());
     return SPTRSV_OK;
 }
 

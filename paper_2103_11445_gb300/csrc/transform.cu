@@ -150,7 +150,7 @@ __global__ void rewrite_count_kernel(int64_t nitems, const int32_t *__restrict__
                                      const int32_t *__restrict__ col,
                                      const int32_t *__restrict__ level, int cap,
                                      int32_t *fill_out, unsigned long long *added,
-                                     int32_t *overflow) {
+                                     int32_t *overflow, int32_t *maxlen) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
@@ -164,8 +164,12 @@ __global__ void rewrite_count_kernel(int64_t nitems, const int32_t *__restrict__
             if (fill_out) fill_out[it] = f;
             if (item_q) {
                 const int32_t q = item_q[it];
-                if (f < 0) atomicExch(&overflow[q], 1);
-                else atomicAdd(&added[q], (unsigned long long)(2ll * (f - (row_ptr[row + 1] - 1 - row_ptr[row]))));
+                if (f < 0) {
+                    atomicExch(&overflow[q], 1);
+                } else {
+                    atomicAdd(&added[q], (unsigned long long)(2ll * (f - (row_ptr[row + 1] - 1 - row_ptr[row]))));
+                    if (maxlen) atomicMax(&maxlen[q], f);
+                }
             }
         }
         __syncwarp();
@@ -574,7 +578,7 @@ cudaError_t launch_rewrite_count(int64_t nitems, const int32_t *item_row,
                                  const int32_t *item_tgt, const int32_t *item_q,
                                  const int32_t *row_ptr, const int32_t *col,
                                  const int32_t *level, int cap, int32_t *fill_out,
-                                 unsigned long long *added, int32_t *overflow,
+                                 unsigned long long *added, int32_t *overflow, int32_t *maxlen,
                                  int num_sms, cudaStream_t s) {
     if (nitems == 0) return cudaSuccess;
     size_t smem;
@@ -587,7 +591,7 @@ cudaError_t launch_rewrite_count(int64_t nitems, const int32_t *item_row,
     if (blocks > cap_blocks) blocks = cap_blocks;
     rewrite_count_kernel<<<(unsigned)blocks, w * 32, smem, s>>>(
         nitems, item_row, item_tgt, item_q, row_ptr, col, level, cap, fill_out, added,
-        overflow);
+        overflow, maxlen);
     return cudaGetLastError();
 }
 
@@ -609,6 +613,66 @@ cudaError_t launch_rewrite_numeric(int64_t nitems, const int32_t *item_row,
     rewrite_numeric_kernel<<<(unsigned)blocks, w * 32, smem, s>>>(
         nitems, item_row, item_tgt, out_off, row_ptr, col, val, level, cap, out_col, out_val,
         nb_out, st);
+    return cudaGetLastError();
+}
+
+namespace {
+// most off-diagonal terms of a row, per level
+__global__ void level_max_kernel(int32_t n, const int32_t *__restrict__ level,
+                                 const int32_t *__restrict__ offdeg, int32_t *out) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicMax(&out[level[i]], offdeg[i]);
+}
+
+// Weighted critical path, one new level of the solve structure per launch
+// (every dependency lies in an earlier level, so its finish time is known):
+// warp per chunk, each lane its entries of one row; x terms (col >= 0) are
+// dependencies, b terms (col in [-n, -1]) and x terms count as the row's
+// terms, unknowns of a CTA-local run (col < -n) are decoded to their row.
+__global__ void critpath_level_kernel(int32_t c0, int32_t c1, int L, int32_t n,
+                                      const int4 *__restrict__ meta,
+                                      const int32_t *__restrict__ ecol,
+                                      const int32_t *__restrict__ row_id,
+                                      const int32_t *__restrict__ chunk_run_p0, int64_t hop,
+                                      int64_t *finish) {
+    const int64_t c = c0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (c >= c1) return;
+    const int4 mt = meta[c];
+    const int k = lane / L, s = lane % L;
+    int64_t terms = 0, dep = 0;
+    if (k < mt.y) {
+        const int64_t stride = (int64_t)mt.y * L;
+        for (int j = s; j < mt.z * L; j += L) {
+            int32_t cc = ecol[mt.w + (int64_t)(j / L) * stride + (int64_t)k * L + (j % L)];
+            if (cc == PAD_COL) continue;
+            ++terms;
+            if (cc < -n && chunk_run_p0) cc = row_id[chunk_run_p0[c] + (-(n + 1) - cc)];
+            if (cc >= 0) dep = max(dep, finish[cc]);
+        }
+    }
+    for (int o = L / 2; o > 0; o >>= 1) {
+        terms += __shfl_xor_sync(FULL_MASK, terms, o);
+        dep = max(dep, __shfl_xor_sync(FULL_MASK, dep, o));
+    }
+    if (k < mt.y && s == 0) finish[row_id[mt.x + k]] = hop + terms + dep;
+}
+}  // namespace
+
+cudaError_t launch_level_max(int32_t n, const int32_t *level, const int32_t *offdeg, int32_t *out,
+                             cudaStream_t s) {
+    if (n > 0) level_max_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, level, offdeg, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_critpath_level(int32_t c0, int32_t c1, int L, int32_t n, const int4 *meta,
+                                  const int32_t *ecol, const int32_t *row_id,
+                                  const int32_t *chunk_run_p0, int64_t hop, int64_t *finish,
+                                  cudaStream_t s) {
+    if (c1 <= c0) return cudaSuccess;
+    const int64_t threads = (int64_t)(c1 - c0) * 32;
+    critpath_level_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+        c0, c1, L, n, meta, ecol, row_id, chunk_run_p0, hop, finish);
     return cudaGetLastError();
 }
 

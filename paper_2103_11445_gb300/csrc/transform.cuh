@@ -14,7 +14,17 @@ cudaError_t launch_rewrite_count(int64_t nitems, const int32_t *item_row,
                                  const int32_t *row_ptr, const int32_t *col,
                                  const int32_t *level, int cap, int32_t *fill_out,
                                  unsigned long long *added, int32_t *overflow,
-                                 int num_sms, cudaStream_t s);
+                                 int32_t *maxlen, int num_sms, cudaStream_t s);
+// out[level] = most off-diagonal terms of a row of that level (out zeroed)
+cudaError_t launch_level_max(int32_t n, const int32_t *level, const int32_t *offdeg, int32_t *out,
+                             cudaStream_t s);
+// finish[row] = hop + terms(row) + max finish of its dependencies, for the
+// rows of chunks [c0, c1) (one level of a solve structure; chunk_run_p0 may
+// be null when no entry encodes a run slot)
+cudaError_t launch_critpath_level(int32_t c0, int32_t c1, int L, int32_t n, const int4 *meta,
+                                  const int32_t *ecol, const int32_t *row_id,
+                                  const int32_t *chunk_run_p0, int64_t hop, int64_t *finish,
+                                  cudaStream_t s);
 cudaError_t launch_rewrite_numeric(int64_t nitems, const int32_t *item_row,
                                    const int32_t *item_tgt, const int64_t *out_off,
                                    const int32_t *row_ptr, const int32_t *col,

@@ -210,9 +210,11 @@ def test_select_auto_keeps_a_timed_candidate():
     info = P.info()
     assert info["select_mode"] == 4
     code = info["chosen_depth"]
-    assert code in (0, 1, 2, 3, 200, 108, 116)
+    assert code in (0, 1, 2, 3, 200, 108, 116, 300)
     if code == 0:
         kw = dict(select_mode=0)
+    elif code == 300:
+        kw = dict(select_mode=5, max_depth=4)
     elif code == 200:
         kw = dict(select_mode=1)
     elif code >= 100:
