@@ -23,6 +23,9 @@ Contents (each function cites the passage of the paper it follows):
 * ``pcg``            preconditioned conjugate gradients with the symmetric
   Gauss-Seidel preconditioner (two triangular solves per step) -- numpy and
   the substitutions above, ``pcg.py``;
+* ``features``       per-level features of the matrix-analysis module (rows,
+  entries, log2 row-length histogram, ancestor span, fill of each lift;
+  Sec. IV) -- Python, ``features.py``;
 * ``critpath``       weighted critical path of a (transformed) system and
   the critical-path-driven segment selection for synchronisation-free
   solves (Sec. III's remark that rewriting applies to them) -- Python,
