@@ -553,6 +553,20 @@ SPTRSV_API sptrsv_status_t sptrsv_last_kernel_ms(sptrsv_plan_t p, float *ms);
  * the injected dependency. */
 SPTRSV_API sptrsv_status_t sptrsv_debug_inject_wait(sptrsv_plan_t p, int32_t row);
 
+/* Per-level features of the analysis (the matrix-analysis module, Sec. IV),
+ * h_feat [nlev][11 + lifts] floats (host), for level l:
+ *   0 rows, 1 off-diagonal entries of its rows,
+ *   2..9 rows by off-diagonal count c in log2 bins: bin 0 c = 0, bin b
+ *        (1..6) 2^(b-1) <= c < 2^b, bin 7 c >= 64,
+ *   10 ancestor span: max over its rows of l - (lowest level it depends on),
+ *   10 + r (r = 1..lifts) FLOPs added when every row of l is rewritten to
+ *        target level l - r (2 per added x or b term), -1 when a row would
+ *        exceed max_row_fill, 0 when l < r.
+ * Counted on the device (the fill columns by the rewriting kernels);
+ * synchronises `stream`.  lifts in 0..16. */
+SPTRSV_API sptrsv_status_t sptrsv_level_features(sptrsv_plan_t p, int32_t lifts,
+                                                 float *h_feat, sptrsv_stream_t stream);
+
 /* Weighted critical path of the plan's current FP64 solve structure (the
  * system the solve kernels run, rewritten rows included): CP = max over rows
  * of f(i) = hop_weight + terms(i) + max f(j) over the unknowns j its x terms

@@ -96,6 +96,7 @@ _SIGS = {
                                          c_void_p]),
     "sptrsv_debug_inject_wait": (c_int32, [c_void_p, c_int32]),
     "sptrsv_critical_path": (c_int32, [c_void_p, c_int32, POINTER(c_int64), c_void_p]),
+    "sptrsv_level_features": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
     "sptrsv_costmodel_features": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "sptrsv_set_costmodel": (c_int32, [c_void_p, c_void_p]),
     "sptrsv_mlp_num_params": (c_int64, [c_int32, c_int32]),
@@ -246,6 +247,14 @@ def sptrsv_get_transformed(plan: int, d_new_level: int, d_xptr: int, d_xcol: int
 
 def sptrsv_debug_inject_wait(plan: int, row: int) -> None:
     _check(load().sptrsv_debug_inject_wait(plan, row), "sptrsv_debug_inject_wait")
+
+
+def sptrsv_level_features(plan: int, nlev: int, lifts: int = 2, stream: int = 0):
+    import numpy as np
+    out = np.zeros((max(nlev, 0), 11 + lifts), dtype=np.float32)
+    _check(load().sptrsv_level_features(plan, lifts, out.ctypes.data, stream),
+           "sptrsv_level_features")
+    return out
 
 
 def sptrsv_critical_path(plan: int, hop_weight: int = 0, stream: int = 0) -> int:

@@ -1759,6 +1759,38 @@ sptrsv_status_t sptrsv_last_kernel_ms(sptrsv_plan_t p, float *ms) {
     return SPTRSV_OK;
 }
 
+sptrsv_status_t sptrsv_level_features(sptrsv_plan_t p, int32_t lifts, float *h_feat,
+                                      sptrsv_stream_t stream) {
+    if (!p || lifts < 0 || lifts > 16 || (p->nlev > 0 && !h_feat)) return SPTRSV_ERR_INVALID_ARG;
+    if (p->latched != SPTRSV_OK) return SPTRSV_ERR_BAD_STATE;
+    const int32_t nlev = p->nlev;
+    if (nlev == 0) return SPTRSV_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<unsigned long long> acc((size_t)nlev * 11);
+    {
+        DevArr<unsigned long long> d;
+        CK(d.alloc(acc.size()));
+        CK(cudaMemsetAsync(d.p, 0, acc.size() * sizeof(unsigned long long), s));
+        CK(launch_level_counts(p->n, p->row_ptr.p, p->col.p, p->level.p, d.p, s));
+        CK(cudaMemcpyAsync(acc.data(), d.p, acc.size() * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    FillQuery fo{p, s, p->prm.max_row_fill, {}};
+    std::vector<std::pair<int32_t, int32_t>> qs;
+    for (int32_t l = 1; l < nlev; ++l)
+        for (int32_t r = 1; r <= std::min(lifts, l); ++r) qs.emplace_back(l, r);
+    CKS(fo.run(qs));
+    const int F = 11 + lifts;
+    for (int32_t l = 0; l < nlev; ++l) {
+        float *f = h_feat + (size_t)l * F;
+        for (int k = 0; k < 11; ++k) f[k] = (float)acc[(size_t)l * 11 + k];
+        for (int r = 1; r <= lifts; ++r)
+            f[10 + r] = r <= l ? (float)fo.cache[{l, r}] : 0.f;   // -1: over the fill cap
+    }
+    return SPTRSV_OK;
+}
+
 sptrsv_status_t sptrsv_critical_path(sptrsv_plan_t p, int32_t hop_weight, int64_t *h_cp,
                                      sptrsv_stream_t stream) {
     if (!p || !h_cp) return SPTRSV_ERR_INVALID_ARG;

@@ -659,6 +659,36 @@ __global__ void critpath_level_kernel(int32_t c0, int32_t c1, int L, int32_t n,
 }
 }  // namespace
 
+namespace {
+// Per-level counts of the analysis features: acc[l][0] rows, [1] entries,
+// [2 + b] rows in log2 length bin b, [10] ancestor span (max).
+__global__ void level_counts_kernel(int32_t n, const int32_t *__restrict__ row_ptr,
+                                    const int32_t *__restrict__ col,
+                                    const int32_t *__restrict__ level,
+                                    unsigned long long *acc) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t a = row_ptr[i], e = row_ptr[i + 1] - 1;   // the diagonal is last
+    const int32_t c = e - a;
+    const int32_t lv = level[i];
+    int32_t lo = lv;
+    for (int32_t k = a; k < e; ++k) lo = min(lo, level[col[k]]);
+    const int bin = c <= 0 ? 0 : min(32 - __clz(c), 7);
+    unsigned long long *q = acc + (int64_t)lv * 11;
+    atomicAdd(&q[0], 1ull);
+    atomicAdd(&q[1], (unsigned long long)c);
+    atomicAdd(&q[2 + bin], 1ull);
+    atomicMax(&q[10], (unsigned long long)(lv - lo));
+}
+}  // namespace
+
+cudaError_t launch_level_counts(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                                const int32_t *level, unsigned long long *acc, cudaStream_t s) {
+    if (n > 0)
+        level_counts_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, row_ptr, col, level, acc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_level_max(int32_t n, const int32_t *level, const int32_t *offdeg, int32_t *out,
                              cudaStream_t s) {
     if (n > 0) level_max_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, level, offdeg, out);

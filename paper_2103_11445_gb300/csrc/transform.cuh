@@ -15,6 +15,10 @@ cudaError_t launch_rewrite_count(int64_t nitems, const int32_t *item_row,
                                  const int32_t *level, int cap, int32_t *fill_out,
                                  unsigned long long *added, int32_t *overflow,
                                  int32_t *maxlen, int num_sms, cudaStream_t s);
+// acc[l][11] (zeroed): rows, off-diagonal entries, 8 log2 length bins and
+// the ancestor span of level l (the per-level analysis features)
+cudaError_t launch_level_counts(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                                const int32_t *level, unsigned long long *acc, cudaStream_t s);
 // out[level] = most off-diagonal terms of a row of that level (out zeroed)
 cudaError_t launch_level_max(int32_t n, const int32_t *level, const int32_t *offdeg, int32_t *out,
                              cudaStream_t s);
