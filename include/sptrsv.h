@@ -432,6 +432,15 @@ SPTRSV_API sptrsv_status_t sptrsv_batch_check(sptrsv_batch_t batch, sptrsv_strea
 SPTRSV_API sptrsv_status_t sptrsv_batch_get_info(sptrsv_batch_t batch, int32_t *h_iters,
                                                  int32_t *h_converged, int32_t *h_cta_count,
                                                  int32_t *h_graph);
+/* Per matrix, the milliseconds its CTA group spent in the last batched solve
+ * (first CTA in to last CTA out, %globaltimer); synchronises with that solve.
+ * SPTRSV_ERR_BAD_STATE before any solve.  The groups are sized so that the
+ * slowest matrix is as fast as it can be: the first solve with a set of
+ * column counts runs once with groups predicted from each matrix's levels
+ * and chunks per level, measures every group, and re-sizes the groups from
+ * the measured times before the graph is captured (that first call solves
+ * twice). */
+SPTRSV_API sptrsv_status_t sptrsv_batch_get_times(sptrsv_batch_t b, float *h_ms);
 SPTRSV_API void sptrsv_batch_destroy(sptrsv_batch_t batch);
 
 /* Preconditioners of sptrsv_pcg_create, both built on A's lower triangle. */

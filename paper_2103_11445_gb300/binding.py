@@ -122,6 +122,7 @@ _SIGS = {
     "sptrsv_batch_check": (c_int32, [c_void_p, c_void_p]),
     "sptrsv_batch_get_info": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sptrsv_batch_destroy": (None, [c_void_p]),
+    "sptrsv_batch_get_times": (c_int32, [c_void_p, c_void_p]),
     "sptrsv_set_profiling": (c_int32, [c_void_p, c_int32]),
     "sptrsv_solve_ir_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "sptrsv_last_kernel_ms": (c_int32, [c_void_p, POINTER(ctypes.c_float)]),
@@ -413,6 +414,12 @@ def sptrsv_batch_get_info(batch: int, count: int):
     g = c_int32()
     _check(load().sptrsv_batch_get_info(batch, it, cv, ct, byref(g)), "sptrsv_batch_get_info")
     return dict(iters=list(it), converged=list(cv), cta_count=list(ct), graph=g.value)
+
+
+def sptrsv_batch_get_times(batch: int, count: int):
+    ms = (ctypes.c_float * count)()
+    _check(load().sptrsv_batch_get_times(batch, ms), "sptrsv_batch_get_times")
+    return list(ms)
 
 
 def sptrsv_batch_destroy(batch: int) -> None:

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <queue>
 #include <vector>
 
 #include "plan.cuh"
@@ -34,6 +35,9 @@ struct sptrsv_batch_s {
     cudaEvent_t done = nullptr;
     bool launched = false;
     sptrsv_status_t latched = SPTRSV_OK;
+    // CTA groups re-sized from the measured times of a first solve, valid for
+    // the column counts they were measured with
+    std::vector<int32_t> tuned_cnt, tuned_nrhs;
     ~sptrsv_batch_s() {
         if (exec) cudaGraphExecDestroy(exec);
         if (done) cudaEventDestroy(done);
@@ -59,29 +63,60 @@ int pow2_at_least(int v) {
     return r;
 }
 
-// Splits `total` CTAs over the matrices in proportion to their bytes
-// (structure + right-hand sides), at least one each.
-bool assign_groups(const std::vector<double> &w, int total, std::vector<int32_t> &cnt) {
-    const int m = (int)w.size();
+// Predicted time of one matrix's solve on w warps, in chunk passes: the
+// levels run one after another and a level of C chunks takes ceil(C / w)
+// passes of the group's warps (its critical path times its width), plus the
+// work that is not tied to levels (refinement sweeps, the copy of x), spread
+// over all w warps; `work` is counted in chunk passes of one warp.
+double predict_passes(const std::vector<int32_t> &lvl_chunk, double work, int64_t w) {
+    double t = 0.0;
+    for (size_t l = 0; l + 1 < lvl_chunk.size(); ++l) {
+        const int64_t c = lvl_chunk[l + 1] - lvl_chunk[l];
+        t += (double)((c + w - 1) / w);
+    }
+    return t + work / (double)w;
+}
+
+// Splits `total` CTAs (warps_per_cta warps each) over the matrices, at least
+// one each, so that the slowest predicted matrix is as fast as it can be:
+// the matrix predicted slowest gets the next CTA while that shortens its
+// time.  CTAs that shorten no matrix go in proportion to `bytes`.
+// `scale` (optional) turns each prediction into time: a matrix measured at
+// t ms on c CTAs gets scale t / predict(c).
+bool assign_groups_by_time(const std::vector<const std::vector<int32_t> *> &lvl,
+                           const std::vector<double> &work, const std::vector<double> &bytes,
+                           int total, int warps_per_cta, std::vector<int32_t> &cnt,
+                           const std::vector<double> *scale = nullptr) {
+    const int m = (int)lvl.size();
     if (m > total) return false;
     cnt.assign(m, 1);
-    double sum = 0.0;
-    for (double v : w) sum += v;
-    int left = total - m;
-    if (sum <= 0.0 || left == 0) return true;
-    std::vector<std::pair<double, int>> frac;
-    int used = 0;
+    std::vector<double> t(m);
+    auto sc = [&](int i) { return scale ? (*scale)[i] : 1.0; };
+    std::priority_queue<std::pair<double, int>> heap;
     for (int i = 0; i < m; ++i) {
-        const double share = w[i] / sum * left;
-        const int extra = (int)std::floor(share);
-        cnt[i] += extra;
-        used += extra;
-        frac.emplace_back(share - extra, i);
+        t[i] = sc(i) * predict_passes(*lvl[i], work[i], warps_per_cta);
+        heap.emplace(t[i], i);
     }
-    std::sort(frac.begin(), frac.end(), [](auto &a, auto &b) { return a.first > b.first; });
-    for (int k = 0; k < left - used && k < m; ++k) cnt[frac[k].second] += 1;
+    int left = total - m;
+    while (left > 0 && !heap.empty()) {
+        const int i = heap.top().second;
+        heap.pop();
+        const double tn =
+            sc(i) * predict_passes(*lvl[i], work[i], (int64_t)(cnt[i] + 1) * warps_per_cta);
+        if (tn >= t[i] - 1e-9) continue;   // saturated: one pass per level already
+        cnt[i] += 1;
+        t[i] = tn;
+        --left;
+        heap.emplace(t[i], i);
+    }
+    if (left > 0) {   // the rest by bytes
+        double sum = 0.0;
+        for (double v : bytes) sum += v;
+        for (int i = 0; i < m && sum > 0.0; ++i) cnt[i] += (int)std::floor(bytes[i] / sum * left);
+    }
     return true;
 }
+
 
 }  // namespace
 
@@ -164,8 +199,22 @@ SPTRSV_API sptrsv_status_t sptrsv_batch_solve(sptrsv_batch_t bt, const double *c
         const int64_t slots = bt->ir ? p->s32.nslots : p->s64.nslots;
         w[i] = (double)slots * (bt->ir ? 8 : 12) + (double)p->n * (16.0 + 16.0 * nrhs[i]);
     }
+    // groups sized by predicted time: levels (critical path) x chunks per level
+    std::vector<const std::vector<int32_t> *> lvl(m);
+    std::vector<double> work(m);
+    for (int32_t i = 0; i < m; ++i) {
+        const sptrsv_plan_t p = bt->plans[i];
+        lvl[i] = bt->ir ? &p->s32.h_lvl_chunk : &p->s64.h_lvl_chunk;
+        // refinement sweeps and copies: about a chunk pass per 32 x 8 row-columns per round
+        const int rounds = bt->ir ? 3 : 1;
+        work[i] = (double)p->n * nrhs[i] * rounds / 256.0;
+    }
     std::vector<int32_t> cnt;
-    if (!assign_groups(w, bt->grid, cnt)) return SPTRSV_ERR_UNSUPPORTED;
+    const std::vector<int32_t> nr_now(nrhs, nrhs + m);
+    const bool tuned = !bt->tuned_cnt.empty() && bt->tuned_nrhs == nr_now;
+    if (tuned) cnt = bt->tuned_cnt;
+    else if (!assign_groups_by_time(lvl, work, w, bt->grid, bt->block_threads / 32, cnt))
+        return SPTRSV_ERR_UNSUPPORTED;
     // the staging table may still be read by the previous launch
     if (bt->launched) BCK(cudaEventSynchronize(bt->done));
     if (bt->ir && off[m] > bt->scratch_elems) {
@@ -174,6 +223,7 @@ SPTRSV_API sptrsv_status_t sptrsv_batch_solve(sptrsv_batch_t bt, const double *c
         bt->scratch_elems = off[m];
         bt->graph_built = false;  // the captured graph points at the old scratch
     }
+    auto fill_table = [&](const std::vector<int32_t> &cnt) {
     int32_t begin = 0;
     for (int32_t i = 0; i < m; ++i) {
         const sptrsv_plan_t p = bt->plans[i];
@@ -200,6 +250,8 @@ SPTRSV_API sptrsv_status_t sptrsv_batch_solve(sptrsv_batch_t bt, const double *c
         M.cta_count = cnt[i];
         begin += cnt[i];
     }
+    };
+    fill_table(cnt);
     auto enqueue = [&](cudaStream_t q) -> cudaError_t {
         cudaError_t e = cudaMemcpyAsync(bt->d_mats.p, bt->h_mats, sizeof(BatchMat) * m,
                                         cudaMemcpyHostToDevice, q);
@@ -209,6 +261,30 @@ SPTRSV_API sptrsv_status_t sptrsv_batch_solve(sptrsv_batch_t bt, const double *c
         return launch_batch(bt->d_mats.p, m, bt->d_ctl.p, bt->st.p, bt->ir, bt->tol, bt->max_iter,
                             bt->timeout_ns, bt->block_threads, bt->grid, q);
     };
+    if (!tuned) {
+        // first solve with these column counts: run it once, measure every
+        // group, and re-size the groups from the measured times
+        BCK(enqueue(s));
+        BCK(cudaStreamSynchronize(s));
+        std::vector<BatchCtl> ctl(m);
+        BCK(cudaMemcpy(ctl.data(), bt->d_ctl.p, sizeof(BatchCtl) * m, cudaMemcpyDeviceToHost));
+        std::vector<double> scale(m, 1.0);
+        const int wpc = bt->block_threads / 32;
+        for (int32_t i = 0; i < m; ++i) {
+            const double ms = ctl[i].t_end > ctl[i].t_begin
+                                  ? (double)(ctl[i].t_end - ctl[i].t_begin) * 1e-6 : 0.0;
+            const double pr = predict_passes(*lvl[i], work[i], (int64_t)cnt[i] * wpc);
+            scale[i] = pr > 0.0 ? ms / pr : 0.0;
+        }
+        std::vector<int32_t> cnt2;
+        if (assign_groups_by_time(lvl, work, w, bt->grid, wpc, cnt2, &scale)) {
+            cnt = cnt2;
+            fill_table(cnt);
+        }
+        bt->tuned_cnt = cnt;
+        bt->tuned_nrhs = nr_now;
+        bt->graph_built = false;   // capture the re-sized table
+    }
     // the legacy default stream cannot be captured: launch directly there
     if (bt->use_graph && s != nullptr && (!bt->graph_built || bt->graph_stream != s)) {
         if (bt->exec) {
@@ -268,6 +344,19 @@ SPTRSV_API sptrsv_status_t sptrsv_batch_get_info(sptrsv_batch_t bt, int32_t *h_i
         if (h_cta_count) h_cta_count[i] = bt->h_mats[i].cta_count;
     }
     if (h_graph) *h_graph = (bt->use_graph && bt->graph_built) ? 1 : 0;
+    return SPTRSV_OK;
+}
+
+SPTRSV_API sptrsv_status_t sptrsv_batch_get_times(sptrsv_batch_t bt, float *h_ms) {
+    if (!bt || !h_ms) return SPTRSV_ERR_INVALID_ARG;
+    const int32_t m = (int32_t)bt->plans.size();
+    if (!bt->launched) return SPTRSV_ERR_BAD_STATE;
+    BCK(cudaEventSynchronize(bt->done));
+    std::vector<BatchCtl> ctl(m);
+    BCK(cudaMemcpy(ctl.data(), bt->d_ctl.p, sizeof(BatchCtl) * m, cudaMemcpyDeviceToHost));
+    for (int32_t i = 0; i < m; ++i)
+        h_ms[i] = ctl[i].t_end > ctl[i].t_begin
+                      ? (float)((double)(ctl[i].t_end - ctl[i].t_begin) * 1e-6) : 0.f;
     return SPTRSV_OK;
 }
 

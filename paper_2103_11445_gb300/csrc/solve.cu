@@ -1119,25 +1119,12 @@ __device__ __forceinline__ void atomic_max_abs(unsigned long long *slot, double 
     if ((threadIdx.x & 31) == 0) atomicMax(slot, (unsigned long long)__double_as_longlong(v));
 }
 
+// One matrix's part of the batched solve, run by the CTAs of its group
+// (j-th of G); returns early (every thread of the CTA alike) on an abort.
 template <bool IR>
-__global__ void __launch_bounds__(kMaxSolveThreads)
-batch_kernel(const BatchMat *__restrict__ mats, int32_t nmats, BatchCtl *ctl, DevStatus *st,
-             double tol, int max_iter, uint64_t timeout_ns) {
-    __shared__ int32_t s_m;
-    if (threadIdx.x == 0) {
-        int32_t lo = 0, hi = nmats - 1;
-        while (lo < hi) {
-            const int32_t mid = (lo + hi + 1) >> 1;
-            if (mats[mid].cta_begin <= (int32_t)blockIdx.x) lo = mid; else hi = mid - 1;
-        }
-        s_m = lo;
-    }
-    __syncthreads();
-    const BatchMat &M = mats[s_m];
-    const int32_t j = (int32_t)blockIdx.x - M.cta_begin;
-    const int32_t G = M.cta_count;
-    if (j < 0 || j >= G || M.n == 0) return;
-    BatchCtl *C = ctl + s_m;
+__device__ __forceinline__ void batch_group(const BatchMat &M, BatchCtl *C, DevStatus *st,
+                                            double tol, int max_iter, uint64_t timeout_ns,
+                                            int32_t j, int32_t G) {
     const int wpb = blockDim.x >> 5;
     const int32_t gw = j * wpb + (threadIdx.x >> 5), nw = G * wpb;
     const int64_t gt = (int64_t)j * blockDim.x + threadIdx.x, gthreads = (int64_t)G * blockDim.x;
@@ -1205,6 +1192,30 @@ batch_kernel(const BatchMat *__restrict__ mats, int32_t nmats, BatchCtl *ctl, De
         C->converged = it < max_iter ? 1 : 0;
     }
 #undef SPTRSV_GSYNC
+}
+
+template <bool IR>
+__global__ void __launch_bounds__(kMaxSolveThreads)
+batch_kernel(const BatchMat *__restrict__ mats, int32_t nmats, BatchCtl *ctl, DevStatus *st,
+             double tol, int max_iter, uint64_t timeout_ns) {
+    __shared__ int32_t s_m;
+    if (threadIdx.x == 0) {
+        int32_t lo = 0, hi = nmats - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (mats[mid].cta_begin <= (int32_t)blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        s_m = lo;
+    }
+    __syncthreads();
+    const BatchMat &M = mats[s_m];
+    const int32_t j = (int32_t)blockIdx.x - M.cta_begin;
+    const int32_t G = M.cta_count;
+    if (j < 0 || j >= G || M.n == 0) return;
+    BatchCtl *C = ctl + s_m;
+    if (threadIdx.x == 0) atomicCAS(&C->t_begin, 0ull, (unsigned long long)globaltimer_ns());
+    batch_group<IR>(M, C, st, tol, max_iter, timeout_ns, j, G);
+    if (threadIdx.x == 0) atomicMax(&C->t_end, (unsigned long long)globaltimer_ns());
 }
 }  // namespace
 

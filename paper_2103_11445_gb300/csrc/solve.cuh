@@ -139,6 +139,7 @@ struct BatchCtl {             // per matrix, zeroed before every launch
     unsigned long long norms[kBatchMaxIter + 1][3];  // |r|, |x| per check; [0][2] = |b|
     int32_t iters;            // corrections applied
     int32_t converged;
+    unsigned long long t_begin, t_end;  // %globaltimer: first CTA in, last CTA out
 };
 
 // ir: FP32 solves + FP64 refinement (plans in SPTRSV_F32_IR precision);

@@ -116,3 +116,41 @@ def test_batch_256_uneven_matrices():
         err = oracle.relerr(x.cpu().numpy()[:, cols], ref)
         assert err <= TOL64, (sp, err)
     B.sptrsv_batch_destroy(h)
+
+
+def test_batch_groups_are_timed_and_resized():
+    """Every group's time of the last solve is reported; the first solve
+    re-sizes the groups from measured times (every matrix keeps at least one
+    CTA, the table never holds more CTAs than the grid), and the solves stay
+    right after the re-sizing."""
+    import torch
+    from paper_2103_11445_gb300 import binding as B
+    mats = [mg.stencil3d(12, seed=1), mg.chain(3000, a=0.5, diag=1.0),
+            mg.thin_tail(20_000, seed=4), mg.stencil2d(30)]
+    plans = []
+    for A in mats:
+        P = B.Plan(A.n, A.row_ptr, A.col, A.val)
+        P.transform(select_mode=1, solve_mode=2, precision=1)
+        plans.append(P)
+    h = B.sptrsv_batch_create([P.handle for P in plans])
+    with pytest.raises(B.SptrsvError):
+        B.sptrsv_batch_get_times(h, len(mats))
+    bs = [torch.as_tensor(mg.rhs_uniform(A.n, seed=i), device="cuda") for i, A in enumerate(mats)]
+    xs = [torch.empty_like(b) for b in bs]
+    s = torch.cuda.Stream()
+    for _ in range(3):
+        B.sptrsv_batch_solve(h, [b.data_ptr() for b in bs], [x.data_ptr() for x in xs],
+                             [1] * len(mats), s.cuda_stream)
+        s.synchronize()
+        assert B.sptrsv_batch_check(h, s.cuda_stream) == 0
+        for A, b, x in zip(mats, bs, xs):
+            assert oracle.relerr(x.cpu().numpy(), oracle.forward_subst(A, b.cpu().numpy())) <= 1e-10
+    ms = B.sptrsv_batch_get_times(h, len(mats))
+    assert all(t > 0 for t in ms)
+    info = B.sptrsv_batch_get_info(h, len(mats))
+    assert min(info["cta_count"]) >= 1
+    # the chain (3000 levels of one row) is the slowest and got the most time
+    assert max(ms) == ms[1]
+    B.sptrsv_batch_destroy(h)
+    for P in plans:
+        P.close()
