@@ -714,14 +714,21 @@ struct Refill {
     __device__ __forceinline__ void operator()() const { ring.fill(sd, sl, c, u0, u1); }
 };
 
-// U steps of one lane's entries from the slot: U gathers in flight together,
-// the terms already computed first, then the late arrivals, all still
-// pending polled together (one round trip per round, not one per term).
-// `hook` runs once the gathers are issued, if still pending (the ring's refill).
+// The L-bit mask of one row's lanes (from bit 0).
+template <int L>
+constexpr unsigned kGroupMask = L >= 32 ? 0xFFFFFFFFu : (1u << (L % 32)) - 1u;
+
+// U steps of one lane's entries from the slot, gathered together: the terms
+// already computed are summed into acc, the others are noted in `pend` (bit
+// j0 + u) -- or, in a chunk wider than 32 steps (`defer` false: a slot holds
+// a few long rows as well as many short ones), waited for on the spot.
+// `hook` runs once the gathers are issued, if still pending (the ring's
+// refill).
 template <typename T, int U, typename Hook>
-__device__ __forceinline__ void staged_steps(const int32_t *scol, const T *sval, int stride,
-                                             T *out, const Ctx &cx, T &acc, bool &bail,
-                                             const Hook &hook, bool &hook_pending) {
+__device__ __forceinline__ void gather_steps(const int32_t *scol, const T *sval, int stride,
+                                             int j0, bool defer, T *out, const Ctx &cx, T &acc,
+                                             uint32_t &pend, bool &bail, const Hook &hook,
+                                             bool &hook_pending) {
     int32_t cc[U];
     typename Bits<T>::U xb[U];
 #pragma unroll
@@ -735,33 +742,91 @@ __device__ __forceinline__ void staged_steps(const int32_t *scol, const T *sval,
         hook();
         hook_pending = false;
     }
-    unsigned pend = 0;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        if (cc[u] >= 0 && xb[u] == Sentinel<T>::bits) pend |= 1u << u;
-        else acc = fma(-sval[u * stride], Bits<T>::from(xb[u]), acc);
-    }
-    if (pend == 0) return;
-    WaitBudget wb(cx.timeout_ns);
-    unsigned it = 0;
-    do {
-        if (cx.backoff_ns) __nanosleep(cx.backoff_ns);
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (pend & (1u << u)) xb[u] = Bits<T>::poll(out + (int64_t)cc[u] * cx.ld);
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if ((pend & (1u << u)) && xb[u] != Sentinel<T>::bits) {
-                acc = fma(-sval[u * stride], Bits<T>::from(xb[u]), acc);
-                pend &= ~(1u << u);
-            }
-        if (pend && (++it & kPollMask) == 0 && wb.expired(cx.st, -2)) {
-            bail = true;
-            return;
+        if (cc[u] >= 0 && xb[u] == Sentinel<T>::bits) {
+            if (defer) pend |= 1u << (j0 + u);
+            else acc = fma(-sval[u * stride],
+                           wait_x<T>(out + (int64_t)cc[u] * cx.ld, cx.st, cx.timeout_ns,
+                                     cx.backoff_ns, bail),
+                           acc);
+        } else {
+            acc = fma(-sval[u * stride], Bits<T>::from(xb[u]), acc);
         }
-    } while (pend);
+    }
 }
 
+// Late terms of the warp's rows, each polled by the row's first lane: `gp`
+// bit q = j * L + s stands for step j of lane s (entry j * stride + s from
+// `scol`/`sval`, the row's own entries; 0 on every other lane).  The rounds
+// are warp-wide, so that one FMA instruction serves every row with an
+// arrival (on this GPU each FP64 instruction holds its pipe for many
+// cycles, however few lanes it has): up to four terms per row are polled
+// together per round, each arrival costs one dependent FMA, and a row is
+// stored in the round its last term lands.
+template <typename T, int L>
+__device__ __forceinline__ void finish_late(const int32_t *scol, const T *sval, int stride,
+                                            uint64_t gp, T *out, const Ctx &cx, T acc,
+                                            bool scaled, const T *sdg, T *dst, bool &bail) {
+    WaitBudget wb(cx.timeout_ns);
+    unsigned it = 0;
+    while (__any_sync(FULL_MASK, gp != 0)) {
+        int bq[4];
+        typename Bits<T>::U xb[4];
+        uint64_t m = gp;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            bq[q] = m ? __ffsll((long long)m) - 1 : -1;
+            m &= m - 1;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (bq[q] >= 0)
+                xb[q] = Bits<T>::poll(out + (int64_t)scol[(bq[q] / L) * stride + bq[q] % L] * cx.ld);
+        const bool had = gp != 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (bq[q] >= 0 && xb[q] != Sentinel<T>::bits) {
+                acc = fma(-sval[(bq[q] / L) * stride + bq[q] % L], Bits<T>::from(xb[q]), acc);
+                gp &= ~(1ull << bq[q]);
+            }
+        if (had && gp == 0)
+            store_x<T, true>(dst, scaled ? acc : div_by_diag<T>(acc, sdg[0], sdg[1]));
+        if (gp && (++it & kPollMask) == 0 && wb.expired(cx.st, -2)) {
+            bail = true;
+            gp = 0;
+        }
+        if (cx.backoff_ns) __nanosleep(cx.backoff_ns);
+    }
+}
+
+// Late terms when a row's pending set does not fit one 64-bit mask (L * z >
+// 64): every lane polls its own, the late partial sums are reduced once more.
+template <typename T, int L>
+__device__ __forceinline__ void finish_late_lanes(const int32_t *scol, const T *sval, int stride,
+                                                  uint32_t pend, T *out, const Ctx &cx, T &acc,
+                                                  bool &bail) {
+    T late = T(0);
+    while (pend) {
+        const int j = __ffs(pend) - 1;
+        const T x = wait_x<T>(out + (int64_t)scol[j * stride] * cx.ld, cx.st, cx.timeout_ns,
+                              cx.backoff_ns, bail);
+        if (bail) break;
+        late = fma(-sval[j * stride], x, late);
+        pend &= pend - 1;
+    }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) late += __shfl_xor_sync(FULL_MASK, late, o);
+    acc += late;
+}
+
+// One staged chunk.  Every gather of every step is issued before anything is
+// waited for; the lanes of a row reduce their early sums while the row still
+// waits; the late terms are then polled by the row's first lane alone, so the
+// row's last dependency is followed by one FMA and the store.  A blob marked
+// scaled (descriptor .w != 0) holds the row's coefficients divided by its
+// diagonal: its value starts as b_i / d_i (computed before any wait) and
+// needs no division at the end.
 template <typename T, int L>
 __device__ __forceinline__ bool chunk_staged(const unsigned char *slot, T *out, const Ctx &cx,
                                              const Refill<T> &refill) {
@@ -770,33 +835,35 @@ __device__ __forceinline__ bool chunk_staged(const unsigned char *slot, T *out, 
     const int4 mt = *reinterpret_cast<const int4 *>(slot);
     const BlobLayout<T> lay(mt.y, mt.z, L);
     const bool active = k < mt.y;
-    T acc = T(0), dg = T(1), dy = T(1);
-    int32_t r = 0;
+    const bool scaled = mt.w != 0;
+    // the row id and the diagonal stay in the slot (read again at the end)
+    const int32_t *srow = reinterpret_cast<const int32_t *>(slot + 16 * lay.rows) + k;
+    const T *sdg = reinterpret_cast<const T *>(slot + 16 * lay.diag) + 2 * k;
+    T acc = T(0);
     bool bail = false;
     if (active && s == 0) {
-        r = reinterpret_cast<const int32_t *>(slot + 16 * lay.rows)[k];
-        const T *sd = reinterpret_cast<const T *>(slot + 16 * lay.diag) + 2 * k;
-        dg = sd[0];
-        dy = sd[1];
-        acc = (T)load_rhs(cx, (int64_t)r * cx.ld);
+        const T b = (T)load_rhs(cx, (int64_t)*srow * cx.ld);
+        acc = scaled ? div_by_diag<T>(b, sdg[0], sdg[1]) : b;
     }
     const int stride = mt.y * L;
-    const int32_t *scol = reinterpret_cast<const int32_t *>(slot + 16 * lay.cols) + k * L + s;
-    const T *sval = reinterpret_cast<const T *>(slot + 16 * lay.vals) + k * L + s;
+    const int32_t *rcol = reinterpret_cast<const int32_t *>(slot + 16 * lay.cols) + k * L;
+    const T *rval = reinterpret_cast<const T *>(slot + 16 * lay.vals) + k * L;
     // every step of the row in as few batches as possible: batches of 5
     // (more spill at 64 registers), the remainder in one batch of its
     // exact size; the first batch issued carries the refill
     bool hook_pending = true;
+    const bool defer = mt.z <= 32;
+    uint32_t pend = 0;
     int j = 0;
     if (active)
         for (; j + 5 <= mt.z; j += 5)
-            staged_steps<T, 5>(scol + j * stride, sval + j * stride, stride, out, cx, acc,
-                                   bail, refill, hook_pending);
+            gather_steps<T, 5>(rcol + s + j * stride, rval + s + j * stride, stride, j, defer,
+                               out, cx, acc, pend, bail, refill, hook_pending);
     switch (active ? mt.z - j : 0) {
 #define SPTRSV_STEPS(UU)                                                                       \
     case UU:                                                                                   \
-        staged_steps<T, UU>(scol + j * stride, sval + j * stride, stride, out, cx, acc,    \
-                                bail, refill, hook_pending);                                    \
+        gather_steps<T, UU>(rcol + s + j * stride, rval + s + j * stride, stride, j, defer,    \
+                            out, cx, acc, pend, bail, refill, hook_pending);                   \
         break;
     SPTRSV_STEPS(1) SPTRSV_STEPS(2) SPTRSV_STEPS(3) SPTRSV_STEPS(4)
 #undef SPTRSV_STEPS
@@ -805,7 +872,28 @@ __device__ __forceinline__ bool chunk_staged(const unsigned char *slot, T *out, 
     if (hook_pending) refill();   // lanes without entries (inactive rows, empty rows)
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
-    if (active && s == 0) store_x<T, true>(out + (int64_t)r * cx.ld, div_by_diag<T>(acc, dg, dy));
+    const bool lead = active && s == 0;
+    T *dst = out + (int64_t)(lead ? *srow : 0) * cx.ld;
+    if (__any_sync(FULL_MASK, pend != 0)) {
+        if (L * mt.z <= 64) {
+            // the row's pending steps, lane by lane, gathered into its first
+            // lane; rows with none are stored at once
+            uint64_t gp = 0;
+            for (int jj = 0; jj < mt.z; ++jj) {
+                const unsigned bal = __ballot_sync(FULL_MASK, (pend >> jj) & 1u);
+                const unsigned mine = (bal >> (k * L)) & kGroupMask<L>;
+                gp |= (uint64_t)mine << (jj * L);
+            }
+            if (!lead) gp = 0;
+            if (lead && gp == 0)
+                store_x<T, true>(dst, scaled ? acc : div_by_diag<T>(acc, sdg[0], sdg[1]));
+            finish_late<T, L>(rcol, rval, stride, gp, out, cx, acc, scaled, sdg, dst, bail);
+            return __any_sync(FULL_MASK, bail);
+        }
+        finish_late_lanes<T, L>(rcol + s, rval + s, stride, active ? pend : 0u, out, cx, acc,
+                                bail);
+    }
+    if (lead) store_x<T, true>(dst, scaled ? acc : div_by_diag<T>(acc, sdg[0], sdg[1]));
     return __any_sync(FULL_MASK, bail);
 }
 
@@ -857,8 +945,10 @@ __device__ __forceinline__ void ring_drain(const StageRing<T> &ring, int cur, in
     __syncwarp();
 }
 
+// 88 registers: the gather batches and the late-term rounds fit without
+// spilling, and five CTAs of 128 threads (or two of 256) stay resident per SM.
 template <typename T, int L>
-__global__ void __launch_bounds__(kMaxSolveThreads, 2)
+__global__ void __maxnreg__(88)
 solve_staged_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, DevStatus *st,
                     uint64_t timeout_ns, int skip_if_converged) {
     if (skip_if_converged && converged(st)) return;
@@ -1231,7 +1321,17 @@ __global__ void blob_units_kernel(int32_t nchunks, int L, const int4 *__restrict
     units[c] = BlobLayout<T>(m.y, m.z, L).units;
 }
 
-// one warp per chunk; the blob array is zeroed beforehand (padding)
+template <typename T> struct MinNormal;
+template <> struct MinNormal<double> { static constexpr double v = 2.2250738585072014e-308; };
+template <> struct MinNormal<float> { static constexpr float v = 1.17549435e-38f; };
+
+// one warp per chunk; the blob array is zeroed beforehand (padding).  The
+// chunk's coefficients are stored divided by their row's diagonal (IEEE
+// division) and the descriptor's .w set to 1, unless a quotient of a
+// non-zero coefficient would leave the normal range (overflow, underflow,
+// a zero, infinite or NaN diagonal, a non-finite coefficient): then the
+// chunk keeps its coefficients as they are (.w = 0) and the kernel divides
+// at the end.
 template <typename T>
 __global__ void blob_fill_kernel(int32_t nchunks, int L, const int4 *__restrict__ meta,
                                  const int32_t *__restrict__ row_id, const T *__restrict__ diag,
@@ -1243,7 +1343,6 @@ __global__ void blob_fill_kernel(int32_t nchunks, int L, const int4 *__restrict_
     const int4 m = meta[c];
     const BlobLayout<T> lay(m.y, m.z, L);
     unsigned char *base = reinterpret_cast<unsigned char *>(blob + bofs[c]);
-    if (lane == 0) *reinterpret_cast<int4 *>(base) = m;
     int32_t *rows = reinterpret_cast<int32_t *>(base + 16 * lay.rows);
     T *dg = reinterpret_cast<T *>(base + 16 * lay.diag);
     int32_t *cols = reinterpret_cast<int32_t *>(base + 16 * lay.cols);
@@ -1251,10 +1350,22 @@ __global__ void blob_fill_kernel(int32_t nchunks, int L, const int4 *__restrict_
     for (int k = lane; k < m.y; k += 32) rows[k] = row_id[m.x + k];
     for (int e = lane; e < 2 * m.y; e += 32) dg[e] = diag[2 * (int64_t)m.x + e];
     const int ne = m.z * m.y * L;
+    const int per_step = m.y * L;
+    bool ok = true;
+    for (int e = lane; e < ne; e += 32) {
+        const T v = eval[(int64_t)m.w + e];
+        if (v == T(0)) continue;
+        const T d = diag[2 * ((int64_t)m.x + (e % per_step) / L)];
+        const T q = v / d;
+        ok = ok && isfinite(q) && fabs(q) >= MinNormal<T>::v;
+    }
+    const bool scaled = __all_sync(0xFFFFFFFFu, ok);
     for (int e = lane; e < ne; e += 32) {
         cols[e] = ecol[(int64_t)m.w + e];
-        vals[e] = eval[(int64_t)m.w + e];
+        const T v = eval[(int64_t)m.w + e];
+        vals[e] = scaled ? v / diag[2 * ((int64_t)m.x + (e % per_step) / L)] : v;
     }
+    if (lane == 0) *reinterpret_cast<int4 *>(base) = make_int4(m.x, m.y, m.z, scaled ? 1 : 0);
 }
 }  // namespace
 

@@ -116,6 +116,41 @@ def test_single_row_and_long_rows():
             assert_close_to_oracle(A, x, b, TOL64)
 
 
+@pytest.mark.parametrize("L", [1, 2, 4, 8, 16])
+def test_staged_slots_of_few_long_rows(L):
+    """Three levels of one long row each (70, 40 and 20 dependencies, nearly
+    all on a 4096-row level just before): each forms a one-row chunk that fits
+    a staging slot however wide it is, so its late terms go every way the
+    staged kernel has -- deferred to the row's first lane (up to 64
+    lane-steps), to every lane (more), or waited for on the spot (a chunk
+    wider than 32 steps)."""
+    rng = np.random.default_rng(40 + L)
+    w = 4096
+    n = 2 * w + 3 + 200
+    cols, vals = [], []
+    for i in range(n):
+        if i < w:
+            c = np.zeros(0, np.int64)
+        elif i < 2 * w:
+            c = np.array([i - w], np.int64)
+        elif i < 2 * w + 3:
+            k = i - 2 * w
+            c = rng.choice(np.arange(w, 2 * w), (70, 39, 19)[k], replace=False)
+            c = np.sort(np.concatenate([c, np.arange(2 * w, i)]))
+        else:
+            c = np.array([i - 3, i - 1], np.int64)
+        cols.append(c.astype(np.int64))
+        vals.append(rng.uniform(-1, 1, c.size) / max(1, c.size))
+    A = mg._from_row_lists(n, cols, vals, 1.5 + rng.uniform(0, 1, n))
+    lv, _ = oracle.levels(A)
+    assert [int(lv[2 * w + k]) for k in range(3)] == [2, 3, 4]
+    P = plan_for(A, **plain(solve_mode=2, lanes_per_row=L))
+    assert P.info()["stage_z"] > 0
+    for seed in range(3):
+        b = mg.rhs_uniform(n, seed=seed)
+        assert_close_to_oracle(A, gpu_solve(P, b), b, TOL64)
+
+
 @pytest.mark.parametrize("mode", B_MODES, ids=B_IDS)
 def test_full_stencil3d_128(mode):
     A = mg.stencil3d(128, seed=2000)
