@@ -169,16 +169,16 @@ typedef struct {
                                 keeps the tail only if faster; none
                                 otherwise), < 0 = never, > 256 = 256. */
     int32_t stage_z;         /* synchronisation-free solve of one right-hand
-                                side: each warp's next chunk of rows (row ids,
-                                diagonals, columns, values) is copied into
-                                shared memory by the bulk-copy engine while
-                                the warp solves the current one, for chunks
-                                whose rows need at most stage_z steps per
-                                lane; wider chunks read global memory.
-                                0 = auto (the width of 99% of the chunks,
-                                capped so that the slots of every resident
-                                warp fit an SM's shared memory), < 0 = off,
-                                > 12 = 12. */
+                                side: each warp's next chunks of rows (row
+                                ids, diagonals, columns, values divided by
+                                the diagonal) are copied into shared memory
+                                by asynchronous copies while the warp solves
+                                the current one, for chunks that fit a slot
+                                sized for stage_z steps per lane; larger
+                                chunks read global memory.  0 = auto (the
+                                width of 99% of the chunks, capped so that
+                                the slots of 16 resident warps fit an SM's
+                                shared memory), < 0 = off, > 24 = 24. */
     int32_t hop_weight;      /* SELECT_CRITPATH: weight of one dependency hop
                                 in units of one term of a row (<= 0: 16) */
 } sptrsv_transform_params_t;

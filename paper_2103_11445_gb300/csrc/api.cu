@@ -632,14 +632,15 @@ int auto_lanes(sptrsv_plan_t p) {
 }
 
 // Staging width of the synchronisation-free one-column solve over ss (0 =
-// not staged): the requested or 99% width, capped so that the slots of the
-// 32 warps an SM can hold fit its shared memory.
+// not staged): the requested or 99% width, capped so that the slots of
+// kStageWarpsPerSM warps fit an SM's shared memory (the staged kernel's
+// registers allow about 20 resident warps per SM).
 template <typename T>
 int stage_width(sptrsv_plan_t p, const SolveStruct<T> &ss) {
     const SolveConfig &c = p->cfg;
     if (!c.syncfree || c.stage_off || p->prm.stage_z < 0 || !ss.built) return 0;
     int z = p->prm.stage_z > 0 ? p->prm.stage_z : ss.width_p99;
-    z = std::min(z, stage_cap_z<T>(ss.L, p->smem_per_sm, 32));
+    z = std::min(z, stage_cap_z<T>(ss.L, p->smem_per_sm, kStageWarpsPerSM));
     return std::max(z, 0);
 }
 
@@ -678,10 +679,18 @@ sptrsv_status_t count_terms(sptrsv_plan_t p, cudaStream_t s) {
     return SPTRSV_OK;
 }
 
-// Records of the single-CTA tail for width limit `rows`: the longest suffix
-// of new levels with at most `rows` rows each (none when shorter than
-// kMinTailLevels levels, or when a row has more than 16 in-tail terms).
+// Records of the single-CTA tail for width limit `rows`.  The tail is the
+// longest suffix of new levels with at most `rows` rows each (none when
+// shorter than kMinTailLevels levels), cut into segments where the level
+// width crosses kTailThinRows for good (both sides at least kMinSegLevels
+// levels): each segment is solved by one CTA after a fold pass, so a
+// segment's rows carry only the terms of its own unknowns.  Segments are
+// taken from the last one back; a row with more than 16 such terms splits
+// its segment around its level (at most kMaxTailSegs segments).
 constexpr int32_t kMinTailLevels = 8;
+constexpr int32_t kMinSegLevels = 64;
+constexpr int32_t kMaxTailSegs = 64;
+constexpr int32_t kTailThinRows = 32;
 constexpr int32_t kTailWindow = 16384;   // shared-memory window of unknowns (128 KiB)
 
 sptrsv_status_t build_tail(sptrsv_plan_t p, int rows, cudaStream_t s) {
@@ -695,70 +704,114 @@ sptrsv_status_t build_tail(sptrsv_plan_t p, int rows, cudaStream_t s) {
     auto hi = [&](int32_t g) {
         return p->h_level_ptr[p->seg_first[g] + p->seg_depth[g] + 1];
     };
-    int32_t g0 = nseg, maxw = 0;
-    while (g0 > 0 && hi(g0 - 1) - lo(g0 - 1) <= rows) {
-        --g0;
-        maxw = std::max(maxw, hi(g0) - lo(g0));
-    }
+    int32_t g0 = nseg;
+    while (g0 > 0 && hi(g0 - 1) - lo(g0 - 1) <= rows) --g0;
     if (nseg - g0 < kMinTailLevels || !ss.built || ss.run_encoded > 0) return SPTRSV_OK;
-    const int32_t P0 = lo(g0), nr = p->n - P0, nl = nseg - g0;
-    const int32_t T = std::max(32, (maxw + 31) / 32 * 32);
-    int32_t c0 = 0;
-    CK(cudaMemcpy(&c0, ss.lvl_chunk.p + g0, sizeof(int32_t), cudaMemcpyDeviceToHost));
-    std::vector<int32_t> tlp(nl + 1);
-    for (int32_t g = 0; g < nl; ++g) tlp[g] = lo(g0 + g) - P0;
-    tlp[nl] = nr;
-    DevArr<int32_t> pos_of, cnt_a, cnt_n, flags;
-    DevArr<int64_t> tmp;
-    CK(upload(t.lp, tlp, s));
-    CK(pos_of.alloc(p->n));
-    CK(cnt_a.alloc(nr));
-    CK(cnt_n.alloc(nr));
-    CK(flags.alloc(2));
-    CK(t.aptr.alloc((size_t)nr + 1));
-    CK(tmp.alloc(scan_tmp_elems(nr)));
-    CK(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int32_t), s));
-    CK(launch_pos_of_row(p->n, ss.row_id.p, pos_of.p, s));
-    CK(launch_tail_count(c0, ss.nchunks, ss.L, p->n, ss.meta.p, ss.ecol.p, pos_of.p, P0,
-                         cnt_a.p, cnt_n.p, flags.p, flags.p + 1, s));
-    CK(exclusive_scan_i32_i64(cnt_a.p, t.aptr.p, nr, tmp.p, s));
-    int32_t hflags[2] = {0, 0};
-    int64_t na = 0;
-    CK(cudaMemcpyAsync(hflags, flags.p, sizeof(hflags), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&na, t.aptr.p + nr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (hflags[1] != 0 || hflags[0] > 16) {   // no tail for this plan
-        t = TailStruct{};
-        t.for_rows = rows;
-        t.built = true;
-        return SPTRSV_OK;
+    // cuts where the width class changes and stays changed
+    std::vector<int32_t> thin_before(nseg - g0 + 1, 0);
+    for (int32_t g = g0; g < nseg; ++g)
+        thin_before[g - g0 + 1] = thin_before[g - g0] + (hi(g) - lo(g) < kTailThinRows);
+    auto thin_in = [&](int32_t a, int32_t b) { return thin_before[b - g0] - thin_before[a - g0]; };
+    std::vector<int32_t> cuts{g0};
+    bool cls = hi(g0) - lo(g0) < kTailThinRows;
+    for (int32_t g = g0 + 1; g + kMinSegLevels <= nseg; ++g) {
+        const bool c = hi(g) - lo(g) < kTailThinRows;
+        if (c == cls || g - cuts.back() < kMinSegLevels) continue;
+        const int32_t nthin = thin_in(g, g + kMinSegLevels);
+        if (c ? nthin == kMinSegLevels : nthin == 0) {
+            cuts.push_back(g);
+            cls = c;
+        }
     }
-    const int32_t K = hflags[0] <= 4 ? 4 : hflags[0] <= 8 ? 8 : 16;
-    CK(t.row.alloc(nr));
-    CK(t.nn.alloc(nr));
-    CK(t.diag.alloc(nr));
-    CK(t.tcol.alloc((size_t)K * nr));
-    CK(t.tval.alloc((size_t)K * nr));
-    CK(t.acol.alloc(na > 0 ? na : 1));
-    CK(t.aval.alloc(na > 0 ? na : 1));
-    CK(t.s0.alloc(nr));
-    CK(launch_tail_fill(c0, ss.nchunks, ss.L, p->n, ss.meta.p, ss.ecol.p, ss.eval.p,
-                        ss.row_id.p, ss.diag.p, ss.chunk_level.p, g0, t.lp.p, pos_of.p, P0,
-                        kTailWindow, T, K, nr, t.aptr.p, t.row.p, t.diag.p, t.nn.p, t.tcol.p,
-                        t.tval.p, t.acol.p, t.aval.p, s));
-    CK(cudaStreamSynchronize(s));
-    t.lev0 = g0;
-    t.c0 = c0;
-    t.P0 = P0;
-    t.nrows = nr;
-    t.nlev = nl;
-    t.K = K;
-    t.T = T;
-    t.W = kTailWindow;
+    cuts.push_back(nseg);
+    const std::vector<int32_t> &lc = ss.h_lvl_chunk;
+    DevArr<int32_t> pos_of, flags;
+    CK(pos_of.alloc(p->n));
+    CK(flags.alloc(2));
+    CK(launch_pos_of_row(p->n, ss.row_id.p, pos_of.p, s));
+    // ranges still to build, the last one on top; a range whose rows have
+    // more than 16 in-segment terms is split around its last level holding
+    // such a row (alone, that level is a segment without in-segment terms:
+    // rows of one level never read each other), and the rest recounted
+    std::vector<std::pair<int32_t, int32_t>> todo;
+    for (size_t j = 0; j + 1 < cuts.size(); ++j) todo.emplace_back(cuts[j], cuts[j + 1]);
+    std::vector<TailSeg> segs;   // last first
+    while (!todo.empty()) {
+        const int32_t ga = todo.back().first, gb = todo.back().second;
+        todo.pop_back();
+        const int32_t P0 = lo(ga), P1 = gb < nseg ? lo(gb) : p->n;
+        const int32_t nr = P1 - P0, nl = gb - ga;
+        const int32_t c0 = lc[ga], c1 = gb < nseg ? lc[gb] : ss.nchunks;
+        int32_t maxw = 0;
+        for (int32_t g = ga; g < gb; ++g) maxw = std::max(maxw, hi(g) - lo(g));
+        TailSeg sg;
+        std::vector<int32_t> tlp(nl + 1);
+        for (int32_t g = 0; g < nl; ++g) tlp[g] = lo(ga + g) - P0;
+        tlp[nl] = nr;
+        DevArr<int32_t> cnt_a, cnt_n;
+        DevArr<int64_t> tmp;
+        CK(upload(sg.lp, tlp, s));
+        CK(cnt_a.alloc(nr));
+        CK(cnt_n.alloc(nr));
+        CK(sg.aptr.alloc((size_t)nr + 1));
+        CK(tmp.alloc(scan_tmp_elems(nr)));
+        CK(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int32_t), s));
+        CK(launch_tail_count(c0, c1, ss.L, p->n, ss.meta.p, ss.ecol.p, pos_of.p, P0, cnt_a.p,
+                             cnt_n.p, flags.p, flags.p + 1, s));
+        CK(exclusive_scan_i32_i64(cnt_a.p, sg.aptr.p, nr, tmp.p, s));
+        int32_t hflags[2] = {0, 0};
+        int64_t na = 0;
+        CK(cudaMemcpyAsync(hflags, flags.p, sizeof(hflags), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&na, sg.aptr.p + nr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (hflags[1] != 0) break;   // run slots: this segment and those before, no tail
+        if (hflags[0] > 16) {
+            if (segs.size() + todo.size() + 3 > (size_t)kMaxTailSegs) break;
+            std::vector<int32_t> hn(nr);
+            CK(cudaMemcpy(hn.data(), cnt_n.p, sizeof(int32_t) * nr, cudaMemcpyDeviceToHost));
+            int32_t plast = nr - 1;
+            while (hn[plast] <= 16) --plast;
+            int32_t gs = ga;   // the level holding position plast
+            while (gs + 1 < gb && lo(gs + 1) - P0 <= plast) ++gs;
+            if (gs > ga) todo.emplace_back(ga, gs);
+            todo.emplace_back(gs, gs + 1);
+            if (gs + 1 < gb) todo.emplace_back(gs + 1, gb);
+            continue;
+        }
+        const int32_t K = hflags[0] <= 4 ? 4 : hflags[0] <= 8 ? 8 : 16;
+        const int32_t T = std::max(32, (maxw + 31) / 32 * 32);
+        CK(sg.row.alloc(nr));
+        CK(sg.nn.alloc(nr));
+        CK(sg.diag.alloc(nr));
+        CK(sg.term.alloc((size_t)K * nr));
+        CK(sg.acol.alloc(na > 0 ? na : 1));
+        CK(sg.aval.alloc(na > 0 ? na : 1));
+        CK(sg.s0.alloc(nr));
+        CK(launch_tail_fill(c0, c1, ss.L, p->n, ss.meta.p, ss.ecol.p, ss.eval.p, ss.row_id.p,
+                            ss.diag.p, ss.chunk_level.p, ga, sg.lp.p, pos_of.p, P0, kTailWindow,
+                            T, K, nr, sg.aptr.p, sg.row.p, sg.diag.p, sg.nn.p, sg.term.p,
+                            sg.acol.p, sg.aval.p, s));
+        CK(cudaStreamSynchronize(s));
+        sg.lev0 = ga;
+        sg.c0 = c0;
+        sg.P0 = P0;
+        sg.nrows = nr;
+        sg.nlev = nl;
+        sg.K = K;
+        sg.T = T;
+        sg.W = kTailWindow;
+        segs.push_back(std::move(sg));
+    }
+    if (segs.empty()) return SPTRSV_OK;
+    std::reverse(segs.begin(), segs.end());
+    t.lev0 = segs.front().lev0;
+    t.c0 = segs.front().c0;
+    for (const TailSeg &sg : segs) t.nlev += sg.nlev;
+    t.segs = std::move(segs);
     return SPTRSV_OK;
 }
 
-TailData tail_view(const TailStruct &t) {
+TailData tail_view(const TailSeg &t) {
     TailData d;
     d.nrows = t.nrows;
     d.nlev = t.nlev;
@@ -767,9 +820,8 @@ TailData tail_view(const TailStruct &t) {
     d.lp = t.lp.p;
     d.row = t.row.p;
     d.nn = t.nn.p;
-    d.tcol = t.tcol.p;
+    d.term = t.term.p;
     d.diag = t.diag.p;
-    d.tval = t.tval.p;
     d.aptr = t.aptr.p;
     d.acol = t.acol.p;
     d.aval = t.aval.p;
@@ -1158,7 +1210,7 @@ sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t 
                 CK(launch_solve<double>(sm, b, x, n, 1, 1, p->cfg.syncfree, lc, p->status.p, tmo,
                                         false, s));
             }
-            CK(launch_tail(tail_view(t), b, x, t.T, s));
+            for (const TailSeg &sg : t.segs) CK(launch_tail(tail_view(sg), b, x, sg.T, s));
             if (p->profiling) {
                 CK(cudaEventRecord(p->prof_ev[1], s));
                 p->prof_valid = true;

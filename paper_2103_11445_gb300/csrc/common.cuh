@@ -16,6 +16,10 @@ constexpr unsigned FULL_MASK = 0xffffffffu;
 // (but not PAD) reads b[~col] (a right-hand-side term of a rewritten row),
 // PAD is a padding slot.
 constexpr int32_t PAD_COL = INT32_MIN;
+// Single-CTA tail records: a row whose coefficients are stored as they are
+// (not divided by its diagonal); the record's count field holds it above
+// the count (bits 0-7) and the mask of terms read from x (bits 8-23).
+constexpr int32_t kTailUnscaled = 1 << 30;
 
 // Device status block of a plan (zeroed at creation):
 //  [0] error code (first one wins), [1] row or index involved,

@@ -95,16 +95,24 @@ struct SolveStruct {
 };
 
 // Records of the single-CTA tail (see TailData in solve.cuh).
-struct TailStruct {
-    int32_t for_rows = 0;    // width limit the records were built for
-    int32_t lev0 = 0;        // first new level of the tail
+struct TailSeg {
+    int32_t lev0 = 0;        // first new level of the segment
     int32_t c0 = 0;          // its first chunk
     int32_t P0 = 0;          // its first solve position
-    int32_t nrows = 0, nlev = 0, K = 0, T = 0, W = 0;   // nlev == 0: no tail
-    DevArr<int32_t> lp, row, nn, tcol, acol;
+    int32_t nrows = 0, nlev = 0, K = 0, T = 0, W = 0;
+    DevArr<int32_t> lp, row, nn, acol;
+    DevArr<int4> term;
     DevArr<double2> diag;
-    DevArr<double> tval, aval, s0;
+    DevArr<double> aval, s0;
     DevArr<int64_t> aptr;
+};
+
+struct TailStruct {
+    int32_t for_rows = 0;    // width limit the records were built for
+    int32_t lev0 = 0;        // first new level of the tail (its first segment's)
+    int32_t c0 = 0;          // its first chunk
+    int32_t nlev = 0;        // levels of all segments (0: no tail)
+    std::vector<TailSeg> segs;   // in solve order
     bool built = false;
 };
 

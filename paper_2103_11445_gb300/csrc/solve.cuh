@@ -81,8 +81,11 @@ cudaError_t launch_blob_fill(int32_t nchunks, int L, const int4 *meta, const int
                              const T *diag, const int32_t *ecol, const T *eval,
                              const int64_t *bofs, uint4 *blob, cudaStream_t s);
 
-// Largest staging width (steps per lane) the kernels accept.
-constexpr int kStageZMax = 12;
+// Largest staging width (steps per lane) the kernels accept (at most 32: a
+// lane notes its late steps in one 32-bit mask).
+constexpr int kStageZMax = 24;
+// Resident warps per SM whose slots the default staging width must fit.
+constexpr int kStageWarpsPerSM = 16;
 // Largest staging width whose slots, for `warps` resident warps of the
 // layout with L lanes per row, fit in `smem_per_sm` bytes of shared memory
 // (with 1 KiB per CTA reserved).

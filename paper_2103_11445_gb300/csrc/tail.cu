@@ -28,17 +28,23 @@ __device__ __forceinline__ double div_diag(double s, double d, double y) {
     return s / d;
 }
 
-// Levels at the end of the order that are at most one CTA wide are solved by
-// one CTA: level l's rows go to threads 0..w-1 with __syncthreads between
-// levels, so a dependency hop stays inside one SM (a shared-memory store and a
-// barrier instead of a store's flight to L2 and a remote poll).  Before it,
-// tail_const_kernel folds every term that reads no tail unknown (the b terms
-// of rewritten rows, unknowns solved before the tail) into one constant per
-// row, over the whole grid.  The tail kernel then adds only in-tail terms:
-// unknowns of the last W solve positions come from a shared-memory window
-// (slot = position mod W), older ones from x through L2.  Each thread loads
-// its records A levels before it needs them (they do not depend on x),
-// so the level-to-level critical path is the arithmetic and the barrier.
+// Runs of levels at the end of the order that are at most one CTA wide are
+// solved by one CTA each (a segment): level l's rows go to threads 0..w-1
+// with __syncthreads between levels, so a dependency hop stays inside one SM
+// (a shared-memory store and a barrier instead of a store's flight to L2 and
+// a remote poll).  Before each segment, tail_const_kernel folds every term
+// that reads no unknown of the segment (b terms of rewritten rows, unknowns
+// solved before it) into one constant per row, over the whole grid.  The
+// segment's kernel then adds only in-segment terms: unknowns of the last W
+// solve positions come from a shared-memory window (slot = position mod W),
+// older ones from x through L2.  Each thread loads its records A levels
+// before it needs them and, one level later, the older unknowns they read
+// (finished by then), so the level-to-level critical path is the row's
+// dependent FMAs on window values and the barrier.  Rows are stored divided
+// by their diagonal: no division is left on that path.  On this GPU every
+// FP64 instruction holds its pipe for many cycles, so a row's terms form one
+// chain of FMAs (a second accumulator would cost an add and gain nothing
+// with one warp per scheduler).
 
 __global__ void tail_const_kernel(TailData td, const double *__restrict__ b,
                                   const double *__restrict__ x) {
@@ -57,7 +63,12 @@ __global__ void tail_const_kernel(TailData td, const double *__restrict__ b,
     acc += __shfl_xor_sync(FULL_MASK, acc, 4);
     acc += __shfl_xor_sync(FULL_MASK, acc, 2);
     acc += __shfl_xor_sync(FULL_MASK, acc, 1);
-    if (r < td.nrows && s == 0) td.s0[r] = __ldg(b + __ldg(&td.row[r])) - acc;
+    if (r < td.nrows && s == 0) {
+        const double br = __ldg(b + __ldg(&td.row[r]));
+        const double2 dy = __ldg(&td.diag[r]);
+        const bool scaled = (__ldg(&td.nn[r]) & kTailUnscaled) == 0;
+        td.s0[r] = (scaled ? div_diag(br, dy.x, dy.y) : br) - acc;
+    }
 }
 
 template <int K>
@@ -65,8 +76,8 @@ struct TailRec {
     int32_t row;   // -1: no row for this thread at this level
     int32_t pos, nn;
     double d, y, s0;
-    int32_t c[K];
-    double v[K];
+    int4 t[K];     // (slot or row, 0, value bits); once resolved, a far term holds
+                   // (its unknown's bits, value bits)
 };
 
 // All loads unconditional on the record's own fields (no load waits on
@@ -85,28 +96,48 @@ __device__ __forceinline__ void tail_load(const TailData &td, int32_t lo, int32_
         R.y = dy.y;
         R.s0 = __ldcg(&td.s0[p]);
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            R.c[k] = __ldg(&td.tcol[(int64_t)k * td.nrows + p]);
-            R.v[k] = __ldg(&td.tval[(int64_t)k * td.nrows + p]);
-        }
+        for (int k = 0; k < K; ++k) R.t[k] = __ldg(&td.term[(int64_t)k * td.nrows + p]);
     }
+}
+
+// The far terms' unknowns (solved at least one level before the thread
+// runs this), read from x into the record.
+template <int K>
+__device__ __forceinline__ void tail_resolve(const double *x, TailRec<K> &R) {
+    if (R.row < 0) return;
+    const int far = (R.nn >> 8) & 0xFFFF;
+    if (!far) return;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        if (far & (1 << k)) {
+            const long long v = __double_as_longlong(__ldcg(x + R.t[k].x));
+            R.t[k].x = (int)(v & 0xFFFFFFFFll);
+            R.t[k].y = (int)(v >> 32);
+        }
+}
+
+__device__ __forceinline__ double lohi(int lo, int hi) {
+    return __longlong_as_double(((long long)hi << 32) | (unsigned)lo);
 }
 
 template <int K>
 __device__ __forceinline__ void tail_row(const TailData &td, const TailRec<K> &R,
                                          double *xs, double *x) {
     if (R.row < 0) return;
-    double s1 = R.s0, s2 = 0.0;
+    const int cnt = R.nn & 0xFF, far = (R.nn >> 8) & 0xFFFF;
+    // every window read issued at once (a far term's field holds value bits:
+    // masked into the window, read and dropped), then one chain of FMAs
+    double xv[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        if (k < R.nn) {
-            const int32_t c = R.c[k];
-            const double xv = c >= 0 ? xs[c] : __ldcg(x + ~c);
-            if (K > 4 && (k & 1)) s2 = fma(-R.v[k], xv, s2);
-            else s1 = fma(-R.v[k], xv, s1);
-        }
+        const double w = xs[R.t[k].x & (td.W - 1)];
+        xv[k] = (far & (1 << k)) ? lohi(R.t[k].x, R.t[k].y) : w;
     }
-    const double v = div_diag(K > 4 ? s1 + s2 : s1, R.d, R.y);
+    double acc = R.s0;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        if (k < cnt) acc = fma(-lohi(R.t[k].z, R.t[k].w), xv[k], acc);
+    const double v = (R.nn & kTailUnscaled) ? div_diag(acc, R.d, R.y) : acc;
     xs[R.pos & (td.W - 1)] = v;
     x[R.row] = v;
 }
@@ -134,6 +165,10 @@ __global__ void __launch_bounds__(256, 1) tail_kernel(TailData td, double *__res
             if (l >= nl) break;   // uniform over the CTA
             tail_row<K>(td, rec[u], tail_xs, x);
             tail_load<K>(td, blo[u], bhi[u], rec[u]);   // level l + A
+            // level l + A - 1, loaded one level ago: its far unknowns are
+            // older than the window, so solved before level l, and have
+            // A - 1 levels to arrive
+            tail_resolve<K>(x, rec[(u + A - 1) % A]);
             const int32_t l2 = l + 2 * A;
             blo[u] = l2 < nl ? __ldg(&td.lp[l2]) : 0;
             bhi[u] = l2 < nl ? __ldg(&td.lp[l2 + 1]) : 0;

@@ -513,7 +513,11 @@ __global__ void tail_count_kernel(int32_t c0, int32_t nchunks, int L, int32_t n,
 
 // The records: a term of row p reading tail position q is near when
 // (start of p's level) - q <= W - T (its window slot is not overwritten
-// before p's level), far (read from x) otherwise.
+// before p's level), far (read from x; bit k of the row's far mask) otherwise.
+// A row's coefficients -- in-tail terms and folded ones -- are stored divided
+// by its diagonal (IEEE division), unless the quotient of a non-zero
+// coefficient leaves the normal range: then the row keeps them as they are
+// and is marked kTailUnscaled.
 __global__ void tail_fill_kernel(int32_t c0, int32_t nchunks, int L, int32_t n,
                                  const int4 *__restrict__ meta, const int32_t *__restrict__ ecol,
                                  const double *__restrict__ eval,
@@ -524,8 +528,8 @@ __global__ void tail_fill_kernel(int32_t c0, int32_t nchunks, int L, int32_t n,
                                  int32_t P0, int32_t W, int32_t T, int32_t K, int32_t nr,
                                  const int64_t *__restrict__ aptr, int32_t *__restrict__ trow,
                                  double2 *__restrict__ tdiag, int32_t *__restrict__ tnn,
-                                 int32_t *__restrict__ tcol, double *__restrict__ tval,
-                                 int32_t *__restrict__ acol, double *__restrict__ aval) {
+                                 int4 *__restrict__ term, int32_t *__restrict__ acol,
+                                 double *__restrict__ aval) {
     const int32_t c = c0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (c >= nchunks) return;
     const int4 mt = meta[c];
@@ -533,32 +537,43 @@ __global__ void tail_fill_kernel(int32_t c0, int32_t nchunks, int L, int32_t n,
     const int32_t lstart = tlp[chunk_level[c] - lev0];
     for (int32_t k = 0; k < mt.y; ++k) {
         const int32_t p = mt.x + k - P0;
+        const double d = diag[2 * (int64_t)(mt.x + k)];
         trow[p] = row_id[mt.x + k];
-        tdiag[p] = make_double2(diag[2 * (int64_t)(mt.x + k)], diag[2 * (int64_t)(mt.x + k) + 1]);
+        tdiag[p] = make_double2(d, diag[2 * (int64_t)(mt.x + k) + 1]);
+        bool scaled = true;
+        for (int32_t t = 0; t < mt.z; ++t)
+            for (int sl = 0; sl < L; ++sl) {
+                const int64_t e = mt.w + t * stride + (int64_t)k * L + sl;
+                const int32_t col = ecol[e];
+                if (col == PAD_COL || col < -n || eval[e] == 0.0) continue;
+                const double q = eval[e] / d;
+                scaled = scaled && isfinite(q) && fabs(q) >= 2.2250738585072014e-308;
+            }
         int64_t ai = aptr[p];
-        int32_t ni = 0;
+        int32_t ni = 0, far = 0;
         for (int32_t t = 0; t < mt.z; ++t)
             for (int sl = 0; sl < L; ++sl) {
                 const int64_t e = mt.w + t * stride + (int64_t)k * L + sl;
                 const int32_t col = ecol[e];
                 if (col == PAD_COL || col < -n) continue;
+                const double v = scaled ? eval[e] / d : eval[e];
                 const int32_t q = col >= 0 ? pos_of[col] - P0 : -1;
                 if (q >= 0) {
-                    const int32_t slot = (lstart - q <= W - T) ? (q & (W - 1)) : ~col;
-                    tcol[(int64_t)ni * nr + p] = slot;
-                    tval[(int64_t)ni * nr + p] = eval[e];
+                    const bool nearby = lstart - q <= W - T;
+                    if (!nearby) far |= 1 << ni;
+                    const long long vb = __double_as_longlong(v);
+                    term[(int64_t)ni * nr + p] = make_int4(nearby ? (q & (W - 1)) : col, 0,
+                                                           (int)(vb & 0xFFFFFFFFll),
+                                                           (int)(vb >> 32));
                     ++ni;
                 } else {
                     acol[ai] = col;
-                    aval[ai] = eval[e];
+                    aval[ai] = v;
                     ++ai;
                 }
             }
-        tnn[p] = ni;
-        for (int32_t j = ni; j < K; ++j) {
-            tcol[(int64_t)j * nr + p] = 0;
-            tval[(int64_t)j * nr + p] = 0.0;
-        }
+        tnn[p] = ni | (far << 8) | (scaled ? 0 : kTailUnscaled);
+        for (int32_t j = ni; j < K; ++j) term[(int64_t)j * nr + p] = make_int4(0, 0, 0, 0);
     }
 }
 
@@ -833,13 +848,13 @@ cudaError_t launch_tail_fill(int32_t c0, int32_t nchunks, int L, int32_t n, cons
                              const double *diag, const int32_t *chunk_level, int32_t lev0,
                              const int32_t *tlp, const int32_t *pos_of, int32_t P0, int32_t W,
                              int32_t T, int32_t K, int32_t nr, const int64_t *aptr,
-                             int32_t *trow, double2 *tdiag, int32_t *tnn, int32_t *tcol,
-                             double *tval, int32_t *acol, double *aval, cudaStream_t s) {
+                             int32_t *trow, double2 *tdiag, int32_t *tnn, int4 *term,
+                             int32_t *acol, double *aval, cudaStream_t s) {
     const int32_t m = nchunks - c0;
     if (m <= 0) return cudaSuccess;
     tail_fill_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(
         c0, nchunks, L, n, meta, ecol, eval, row_id, diag, chunk_level, lev0, tlp, pos_of, P0, W,
-        T, K, nr, aptr, trow, tdiag, tnn, tcol, tval, acol, aval);
+        T, K, nr, aptr, trow, tdiag, tnn, term, acol, aval);
     return cudaGetLastError();
 }
 

@@ -69,10 +69,12 @@ cudaError_t launch_encode_runs(int32_t n, int L, const int32_t *row_id, const in
                                int32_t nrc, const int32_t *run_chunk, const int2 *run_span,
                                int32_t *pos_tmp, int32_t *ecol, cudaStream_t s);
 
-// Single-CTA tail (solve.cuh TailData): pos[row_id[i]] = i; per tail row the
-// counts of folded and in-tail terms (chunks c0..nchunks-1, rows numbered
-// from solve position P0), the largest in-tail count in *kmax, *bad = 1 if
-// an entry is a run slot; then the records.
+// Single-CTA tail segments (tail.cuh TailData): pos[row_id[i]] = i; per
+// segment row the counts of folded and in-segment terms (chunks
+// c0..nchunks-1, rows numbered from solve position P0), the largest
+// in-segment count in *kmax, *bad = 1 if an entry is a run slot; then the
+// records (terms packed as (slot or column, 0, value bits), coefficients
+// divided by the diagonal unless a row is marked kTailUnscaled).
 cudaError_t launch_pos_of_row(int32_t n, const int32_t *row_id, int32_t *pos, cudaStream_t s);
 cudaError_t launch_tail_count(int32_t c0, int32_t nchunks, int L, int32_t n, const int4 *meta,
                               const int32_t *ecol, const int32_t *pos_of, int32_t P0,
@@ -83,7 +85,7 @@ cudaError_t launch_tail_fill(int32_t c0, int32_t nchunks, int L, int32_t n, cons
                              const double *diag, const int32_t *chunk_level, int32_t lev0,
                              const int32_t *tlp, const int32_t *pos_of, int32_t P0, int32_t W,
                              int32_t T, int32_t K, int32_t nr, const int64_t *aptr,
-                             int32_t *trow, double2 *tdiag, int32_t *tnn, int32_t *tcol,
-                             double *tval, int32_t *acol, double *aval, cudaStream_t s);
+                             int32_t *trow, double2 *tdiag, int32_t *tnn, int4 *term,
+                             int32_t *acol, double *aval, cudaStream_t s);
 
 }  // namespace sptrsv
