@@ -63,8 +63,10 @@ typedef enum {
     SPTRSV_ERR_TIMEOUT = 8,       /* a bounded device wait gave up */
     SPTRSV_ERR_BAD_STATE = 9,     /* call out of order or plan already failed */
     SPTRSV_ERR_UNSUPPORTED = 10,  /* size or mode the library does not handle */
-    SPTRSV_ERR_BREAKDOWN = 11     /* an iteration met a non-finite residual or a
+    SPTRSV_ERR_BREAKDOWN = 11,    /* an iteration met a non-finite residual or a
                                      non-positive curvature (p, A p) */
+    SPTRSV_ERR_CODEGEN = 12       /* generated code requested but the runtime
+                                     compiler is missing or rejected it */
 } sptrsv_status_t;
 
 typedef struct sptrsv_plan_s *sptrsv_plan_t;    /* opaque, owned by the library */
@@ -181,6 +183,19 @@ typedef struct {
                                 shared memory), < 0 = off, > 24 = 24. */
     int32_t hop_weight;      /* SELECT_CRITPATH: weight of one dependency hop
                                 in units of one term of a row (<= 0: 16) */
+    int32_t codegen_rows;    /* per-matrix generated code (the GPU form of the
+                                paper's specialised code generation, Sec. IV):
+                                a segment of the single-CTA tail (tail_rows >
+                                0) with at most codegen_rows rows and fewer
+                                than 16 terms per level on average is solved
+                                by a kernel generated for it, its row ids,
+                                unknown slots and coefficients written into
+                                the code as constants, compiled at transform
+                                time by the runtime compiler (NVRTC) and run
+                                by one thread in solve order, without
+                                barriers (thin segments: chains, two-row
+                                levels).  0 = off (default); at most 4096
+                                (compiling takes about 1.3 ms per row). */
 } sptrsv_transform_params_t;
 
 /* Everything a caller may want to report about a plan. */
@@ -213,6 +228,9 @@ typedef struct {
     int32_t tail_levels;     /* levels it solves */
     int32_t stage_z;         /* staging width of the FP64 one-column solve in
                                 use (0: not staged) */
+    int32_t codegen_segments; /* tail segments solved by generated kernels */
+    double codegen_ms;       /* time the last transform spent generating and
+                                compiling them */
 } sptrsv_info_t;
 
 SPTRSV_API const char *sptrsv_status_string(sptrsv_status_t s);

@@ -22,7 +22,7 @@ SPTRSV_OK = 0
 STATUS_NAMES = {
     0: "OK", 1: "INVALID_ARG", 2: "NOT_LOWER", 3: "UNSORTED", 4: "ZERO_DIAG",
     5: "MISSING_DIAG", 6: "OOM", 7: "CUDA", 8: "TIMEOUT", 9: "BAD_STATE",
-    10: "UNSUPPORTED", 11: "BREAKDOWN",
+    10: "UNSUPPORTED", 11: "BREAKDOWN", 12: "CODEGEN",
 }
 SELECT_NONE, SELECT_HEURISTIC, SELECT_COSTMODEL, SELECT_FIXED, SELECT_AUTO, SELECT_CRITPATH = \
     0, 1, 2, 3, 4, 5
@@ -49,6 +49,7 @@ class TransformParams(Structure):
         ("cta_run_rows", c_int32), ("wait_timeout_ms", c_int32),
         ("grid_blocks", c_int32), ("poll_backoff_ns", c_int32), ("nrhs_hint", c_int32),
         ("tail_rows", c_int32), ("stage_z", c_int32), ("hop_weight", c_int32),
+        ("codegen_rows", c_int32),
     ]
 
 
@@ -65,7 +66,7 @@ class Info(Structure):
         ("chosen_depth", c_int32),
         ("analyze_ms", c_double), ("transform_ms", c_double), ("op", c_int32),
         ("tuned_from_cache", c_int32), ("tail_rows", c_int32), ("tail_levels", c_int32),
-        ("stage_z", c_int32),
+        ("stage_z", c_int32), ("codegen_segments", c_int32), ("codegen_ms", c_double),
     ]
 
     def as_dict(self) -> dict:

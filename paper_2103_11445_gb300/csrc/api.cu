@@ -11,6 +11,7 @@
 #include <tuple>
 #include <utility>
 
+#include "codegen.cuh"
 #include "plan.cuh"
 #include "tail.cuh"
 
@@ -811,23 +812,6 @@ sptrsv_status_t build_tail(sptrsv_plan_t p, int rows, cudaStream_t s) {
     return SPTRSV_OK;
 }
 
-TailData tail_view(const TailSeg &t) {
-    TailData d;
-    d.nrows = t.nrows;
-    d.nlev = t.nlev;
-    d.K = t.K;
-    d.W = t.W;
-    d.lp = t.lp.p;
-    d.row = t.row.p;
-    d.nn = t.nn.p;
-    d.term = t.term.p;
-    d.diag = t.diag.p;
-    d.aptr = t.aptr.p;
-    d.acol = t.acol.p;
-    d.aval = t.aval.p;
-    d.s0 = t.s0.p;
-    return d;
-}
 
 // Level-major chunk schedule of the synchronisation-free kernels for nw
 // warps, the autotuner's alternative to dealing the chunk list round robin:
@@ -897,6 +881,16 @@ sptrsv_status_t apply_config(sptrsv_plan_t p, cudaStream_t s) {
     if (!f32 && runs <= 0 && p->cfg.tail_rows > 0 && !p->injected &&
         (!p->tail.built || p->tail.for_rows != p->cfg.tail_rows))
         CKS(build_tail(p, p->cfg.tail_rows, s));
+    // generated kernels for the tail's thin segments
+    if (!f32 && p->tail.built && !p->tail.segs.empty() && p->prm.codegen_rows > 0 &&
+        p->tail.gen_rows != p->prm.codegen_rows) {
+        p->tail.gen_ms = 0;
+        for (TailSeg &sg : p->tail.segs) {
+            if (codegen_eligible(sg, p->prm.codegen_rows)) CKS(codegen_build(sg, p->tail.gen_ms));
+            else sg.gen.reset();
+        }
+        p->tail.gen_rows = p->prm.codegen_rows;
+    }
     // schedule and chunk blobs of the synchronisation-free kernels
     if (p->cfg.syncfree) {
         const int32_t nw = grid_for(p, 1, f32) * (p->cfg.block_threads / 32);
@@ -1178,6 +1172,8 @@ void resolve_params(sptrsv_plan_t p, const sptrsv_transform_params_t *in) {
     if (q.nrhs_hint < 1) q.nrhs_hint = 1;
     if (q.nrhs_hint > 32) q.nrhs_hint = 32;
     if (q.tail_rows > 256) q.tail_rows = 256;
+    if (q.codegen_rows < 0) q.codegen_rows = 0;
+    if (q.codegen_rows > kCodegenMaxRows) q.codegen_rows = kCodegenMaxRows;
     if (q.stage_z > kStageZMax) q.stage_z = kStageZMax;
     p->prm = q;
     p->thin_rows_used = q.thin_rows;
@@ -1210,7 +1206,10 @@ sptrsv_status_t solve_impl(sptrsv_plan_t p, const double *b, double *x, int32_t 
                 CK(launch_solve<double>(sm, b, x, n, 1, 1, p->cfg.syncfree, lc, p->status.p, tmo,
                                         false, s));
             }
-            for (const TailSeg &sg : t.segs) CK(launch_tail(tail_view(sg), b, x, sg.T, s));
+            for (const TailSeg &sg : t.segs) {
+                if (sg.gen.fn && t.gen_rows == p->prm.codegen_rows) CK(codegen_launch(sg, b, x, s));
+                else CK(launch_tail(tail_view(sg), b, x, sg.T, s));
+            }
             if (p->profiling) {
                 CK(cudaEventRecord(p->prof_ev[1], s));
                 p->prof_valid = true;
@@ -1377,6 +1376,7 @@ const char *sptrsv_status_string(sptrsv_status_t s) {
     case SPTRSV_ERR_BAD_STATE: return "plan in a bad state (call order or earlier failure)";
     case SPTRSV_ERR_UNSUPPORTED: return "unsupported size or mode";
     case SPTRSV_ERR_BREAKDOWN: return "iteration breakdown (non-finite residual or curvature <= 0)";
+    case SPTRSV_ERR_CODEGEN: return "generated code: runtime compiler missing or source rejected";
     }
     return "unknown status";
 }
@@ -1693,6 +1693,10 @@ sptrsv_status_t sptrsv_get_info(sptrsv_plan_t p, sptrsv_info_t *o) {
     o->tuned_from_cache = p->tuned_from_cache ? 1 : 0;
     o->tail_rows = tail_active(p, 1) ? p->cfg.tail_rows : 0;
     o->tail_levels = tail_active(p, 1) ? p->tail.nlev : 0;
+    o->codegen_segments = 0;
+    if (tail_active(p, 1) && p->tail.gen_rows == p->prm.codegen_rows)
+        for (const TailSeg &sg : p->tail.segs) o->codegen_segments += sg.gen.fn != nullptr;
+    o->codegen_ms = p->tail.gen_ms;
     o->stage_z = p->prm.precision == SPTRSV_F32_IR ? 0 : stage_width(p, p->s64);
     if (p->status.p) {
         DevStatus h;

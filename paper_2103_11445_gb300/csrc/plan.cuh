@@ -95,6 +95,37 @@ struct SolveStruct {
 };
 
 // Records of the single-CTA tail (see TailData in solve.cuh).
+// A kernel generated for one tail segment (the runtime compiler's output,
+// loaded as a library; unloaded with its owner).
+struct GenKernel {
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t fn = nullptr;
+    size_t smem = 0;
+    GenKernel() = default;
+    GenKernel(const GenKernel &) = delete;
+    GenKernel &operator=(const GenKernel &) = delete;
+    GenKernel(GenKernel &&o) noexcept { swap(o); }
+    GenKernel &operator=(GenKernel &&o) noexcept {
+        if (this != &o) {
+            reset();
+            swap(o);
+        }
+        return *this;
+    }
+    ~GenKernel() { reset(); }
+    void reset() {
+        if (lib) cudaLibraryUnload(lib);
+        lib = nullptr;
+        fn = nullptr;
+        smem = 0;
+    }
+    void swap(GenKernel &o) {
+        std::swap(lib, o.lib);
+        std::swap(fn, o.fn);
+        std::swap(smem, o.smem);
+    }
+};
+
 struct TailSeg {
     int32_t lev0 = 0;        // first new level of the segment
     int32_t c0 = 0;          // its first chunk
@@ -105,6 +136,7 @@ struct TailSeg {
     DevArr<double2> diag;
     DevArr<double> aval, s0;
     DevArr<int64_t> aptr;
+    GenKernel gen;           // generated kernel of the segment (fn null: none)
 };
 
 struct TailStruct {
@@ -114,6 +146,8 @@ struct TailStruct {
     int32_t nlev = 0;        // levels of all segments (0: no tail)
     std::vector<TailSeg> segs;   // in solve order
     bool built = false;
+    int32_t gen_rows = 0;    // codegen_rows the generated kernels were made for
+    double gen_ms = 0;       // time spent generating and compiling them
 };
 
 struct SolveConfig {

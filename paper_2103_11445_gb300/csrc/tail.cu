@@ -4,6 +4,8 @@
 // constants; here each thread's records are loaded ahead of need instead).
 #include "tail.cuh"
 
+#include "plan.cuh"
+
 namespace sptrsv {
 namespace {
 
@@ -179,14 +181,20 @@ __global__ void __launch_bounds__(256, 1) tail_kernel(TailData td, double *__res
 
 }  // namespace
 
+cudaError_t launch_tail_fold(const TailData &td, const double *b, const double *x,
+                             cudaStream_t s) {
+    if (td.nrows == 0) return cudaSuccess;
+    const int64_t thr = (int64_t)td.nrows * 8;
+    tail_const_kernel<<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(td, b, x);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tail(const TailData &td, const double *b, double *x, int block_threads,
                         cudaStream_t s) {
     if (td.nrows == 0 || td.nlev == 0) return cudaSuccess;
     if (block_threads < 32 || block_threads > 256 || (td.W & (td.W - 1)) != 0)
         return cudaErrorInvalidValue;
-    const int64_t thr = (int64_t)td.nrows * 8;
-    tail_const_kernel<<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(td, b, x);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_tail_fold(td, b, x, s);
     if (e != cudaSuccess) return e;
     const void *k = td.K <= 4   ? (const void *)tail_kernel<4, 4>
                     : td.K <= 8 ? (const void *)tail_kernel<8, 3>
@@ -198,6 +206,25 @@ cudaError_t launch_tail(const TailData &td, const double *b, double *x, int bloc
     TailData tc = td;
     void *args[] = {(void *)&tc, (void *)&x};
     return cudaLaunchKernel(k, dim3(1), dim3(block_threads), args, smem, s);
+}
+
+// The view of a segment the tail kernels take.
+TailData tail_view(const TailSeg &t) {
+    TailData d;
+    d.nrows = t.nrows;
+    d.nlev = t.nlev;
+    d.K = t.K;
+    d.W = t.W;
+    d.lp = t.lp.p;
+    d.row = t.row.p;
+    d.nn = t.nn.p;
+    d.term = t.term.p;
+    d.diag = t.diag.p;
+    d.aptr = t.aptr.p;
+    d.acol = t.acol.p;
+    d.aval = t.aval.p;
+    d.s0 = t.s0.p;
+    return d;
 }
 
 }  // namespace sptrsv

@@ -33,5 +33,8 @@ struct TailData {
 // the segment; one right-hand side, FP64.
 cudaError_t launch_tail(const TailData &td, const double *b, double *x, int block_threads,
                         cudaStream_t s);
+// The fold pass alone (s0 of every segment row).
+cudaError_t launch_tail_fold(const TailData &td, const double *b, const double *x,
+                             cudaStream_t s);
 
 }  // namespace sptrsv
