@@ -404,9 +404,10 @@ def oracle_relerr_ok(x, b, A, tol: float = 1e-10) -> bool:
 
 
 def sub_results(args) -> dict:
-    """The other two single-GPU workloads (thin tail, batch256), run before
-    the headline so that the headline's timed loops end the run."""
-    out = {"thin_tail": thin_tail_sub(args)}
+    """The other single-GPU workloads (thin tail, batch256, the generated
+    kernel of a small thin matrix), run before the headline so that the
+    headline's timed loops end the run."""
+    out = {"thin_tail": thin_tail_sub(args), "codegen": codegen_sub(args)}
     sub = argparse.Namespace(**vars(args))
     sub.steps, sub.warmup, sub.cpu_seconds = 5, 2, 3.0
     bl = run_batch(sub, 1, 0, emit=False)
@@ -747,6 +748,72 @@ def thin_tail_sub(args):
                          "sample": f"{len(ts)} serial FP64 forward substitutions (median), "
                                    f"C oracle, 1 of {len(os.sched_getaffinity(0))} host cores"},
         "gpu_over_one_core": round(cpu_ms / ms, 3),
+        "relerr_vs_oracle": oracle.relerr(x_gpu, x_ref),
+    }
+
+
+def codegen_sub(args):
+    """A small thin matrix (4,096 rows in single-row levels: each row reads
+    the row before and three random earlier ones) solved three ways: the
+    synchronisation-free kernel, the record-driven single-CTA tail, and the
+    tail's kernel generated for this matrix (codegen_rows); timed like the
+    headline, checked against the oracle, the oracle timed beside it."""
+    import torch
+    import matgen as mg
+    import oracle
+    from paper_2103_11445_gb300 import binding as Bd
+    dev = torch.device("cuda", torch.cuda.current_device())
+    A = mg.thin_tail(4096, seed=5, chain_frac=1.0)
+    b_np = mg.rhs_uniform(A.n, seed=6)
+    B = b_alg(A.n, A.nnz)
+    P = Bd.Plan(A.n, A.row_ptr, A.col, A.val)
+    b = torch.as_tensor(b_np, device=dev)
+    x = torch.empty_like(b)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(steps=10, warm=3):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for _ in range(warm):
+            flush.zero_()
+            P.solve(b, x)
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record()
+            P.solve(b, x)
+            e1.record()
+        torch.cuda.synchronize()
+        P.check()
+        return statistics.mean(a.elapsed_time(c) for a, c in ev)
+
+    base = dict(select_mode=Bd.SELECT_NONE, solve_mode=Bd.SOLVE_SYNCFREE, lanes_per_row=1)
+    P.transform(**base, tail_rows=-1)
+    sf_ms = timed()
+    P.transform(**base, tail_rows=32)
+    tail_ms = timed()
+    t0 = time.perf_counter()
+    P.transform(**base, tail_rows=32, codegen_rows=4096)
+    tr_ms = (time.perf_counter() - t0) * 1e3
+    info = P.info()
+    ms = timed()
+    x_gpu = x.cpu().numpy()
+    x_ref, ts = oracle_solve_timed(A, b_np, 1.0)
+    cpu_ms = statistics.median(ts) * 1e3
+    P.close()
+    gbs = B / (ms * 1e-3) / 1e9
+    return {
+        "workload": f"thin_chain_4096 (n={A.n}, nnz={A.nnz}, {info['nlev']} single-row levels, "
+                    "each row: the row before + 3 random earlier ones; 1 RHS)",
+        "ms": round(ms, 4), "value": round(gbs, 3), "unit": "GB/s",
+        "generated_segments": info["codegen_segments"],
+        "codegen_ms": round(info["codegen_ms"], 1), "transform_ms": round(tr_ms, 1),
+        "record_driven_tail_ms": round(tail_ms, 4), "syncfree_ms": round(sf_ms, 4),
+        "speedup_vs_record_driven_tail": round(tail_ms / ms, 3),
+        "speedup_vs_syncfree": round(sf_ms / ms, 3),
+        "cpu_baseline": {"ms": round(cpu_ms, 4), "value": round(B / (cpu_ms * 1e-3) / 1e9, 4),
+                         "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{len(ts)} serial FP64 forward substitutions (median), "
+                                   f"C oracle, 1 of {len(os.sched_getaffinity(0))} host cores"},
         "relerr_vs_oracle": oracle.relerr(x_gpu, x_ref),
     }
 
