@@ -1320,12 +1320,15 @@ sptrsv_status_t select_auto(sptrsv_plan_t p, const sptrsv_transform_params_t *pr
     double best_ms = 1e30;
     int best = 0;
     sptrsv_status_t st = SPTRSV_OK;
+    // each candidate timed in one layout, 2 lanes per row on 128-thread
+    // CTAs: the best or within a few per cent of the best of the staged
+    // kernel on every plan measured; the winner is then tuned in full
     for (size_t i = 0; i < cands.size() && st == SPTRSV_OK; ++i) {
-        for (int L : {1, 4}) {
+        for (int L : {2}) {
             sptrsv_transform_params_t q = cands[i].q;
             q.solve_mode = SPTRSV_SOLVE_SYNCFREE;
             q.lanes_per_row = L;
-            q.block_threads = 256;
+            q.block_threads = 128;
             q.grid_blocks = 0;
             q.tail_rows = -1;
             if ((st = sptrsv_transform(p, &q, stream)) != SPTRSV_OK) break;
