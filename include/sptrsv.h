@@ -603,6 +603,18 @@ SPTRSV_API sptrsv_status_t sptrsv_level_features(sptrsv_plan_t p, int32_t lifts,
 SPTRSV_API sptrsv_status_t sptrsv_critical_path(sptrsv_plan_t p, int32_t hop_weight,
                                                 int64_t *h_cp, sptrsv_stream_t stream);
 
+/* Source of the kernel generated for tail segment `seg` (0-based, solve
+ * order) of the plan's current configuration (codegen_rows, Sec. IV's
+ * specialised code): the CUDA C++ text the runtime compiler was given, so
+ * that a caller can see the matrix's row ids, unknown slots and
+ * coefficients written into it.  Writes at most `cap` bytes including the
+ * terminating zero into `buf` (host, may be null when cap is 0) and the full
+ * length without the zero into *len.  SPTRSV_ERR_BAD_STATE when the segment
+ * has no generated kernel, SPTRSV_ERR_INVALID_ARG for a bad segment index or
+ * a null `len`. */
+SPTRSV_API sptrsv_status_t sptrsv_codegen_source(sptrsv_plan_t p, int32_t seg, char *buf,
+                                                 size_t cap, size_t *len);
+
 #ifdef __cplusplus
 }
 #endif

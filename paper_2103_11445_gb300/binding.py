@@ -13,8 +13,8 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
-from ctypes import (POINTER, Structure, byref, c_char_p, c_double, c_int32,
-                    c_int64, c_void_p)
+from ctypes import (byref, c_char_p, c_double, c_int32, c_int64, c_size_t, c_void_p,
+                    create_string_buffer, POINTER, Structure)
 
 from . import _build
 
@@ -97,6 +97,8 @@ _SIGS = {
                                          c_void_p]),
     "sptrsv_debug_inject_wait": (c_int32, [c_void_p, c_int32]),
     "sptrsv_critical_path": (c_int32, [c_void_p, c_int32, POINTER(c_int64), c_void_p]),
+    "sptrsv_codegen_source": (c_int32, [c_void_p, c_int32, c_char_p, c_size_t,
+                                        POINTER(c_size_t)]),
     "sptrsv_level_features": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
     "sptrsv_costmodel_features": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "sptrsv_set_costmodel": (c_int32, [c_void_p, c_void_p]),
@@ -264,6 +266,15 @@ def sptrsv_critical_path(plan: int, hop_weight: int = 0, stream: int = 0) -> int
     _check(load().sptrsv_critical_path(plan, hop_weight, byref(cp), stream),
            "sptrsv_critical_path")
     return cp.value
+
+
+def sptrsv_codegen_source(plan: int, seg: int) -> str:
+    n = c_size_t()
+    _check(load().sptrsv_codegen_source(plan, seg, None, 0, byref(n)), "sptrsv_codegen_source")
+    buf = create_string_buffer(n.value + 1)
+    _check(load().sptrsv_codegen_source(plan, seg, buf, n.value + 1, byref(n)),
+           "sptrsv_codegen_source")
+    return buf.value.decode()
 
 
 def sptrsv_solve_ir_noalloc(plan: int, d_b: int, d_x: int, nrhs: int,
@@ -545,6 +556,10 @@ class Plan:
 
     def segments(self):
         return sptrsv_get_segments(self._handle, self.info()["nlev_new"])
+
+    def codegen_source(self, seg: int = 0) -> str:
+        """Source of the kernel generated for tail segment seg."""
+        return sptrsv_codegen_source(self._handle, seg)
 
     def transformed(self):
         """The transformed rows in original order (see sptrsv_get_transformed)."""

@@ -1850,6 +1850,26 @@ sptrsv_status_t sptrsv_level_features(sptrsv_plan_t p, int32_t lifts, float *h_f
     return SPTRSV_OK;
 }
 
+sptrsv_status_t sptrsv_codegen_source(sptrsv_plan_t p, int32_t seg, char *buf, size_t cap,
+                                      size_t *len) {
+    if (!p || !len || seg < 0) return SPTRSV_ERR_INVALID_ARG;
+    if (p->latched != SPTRSV_OK) return SPTRSV_ERR_BAD_STATE;
+    if (!p->tail.built || (size_t)seg >= p->tail.segs.size()) return SPTRSV_ERR_INVALID_ARG;
+    const TailSeg &sg = p->tail.segs[seg];
+    if (!sg.gen.fn || p->tail.gen_rows != p->prm.codegen_rows) return SPTRSV_ERR_BAD_STATE;
+    std::string src;
+    bool thin = false;
+    CKS(codegen_source(sg, src, thin));
+    if (!thin) return SPTRSV_ERR_BAD_STATE;
+    *len = src.size();
+    if (buf && cap > 0) {
+        const size_t k = std::min(cap - 1, src.size());
+        std::memcpy(buf, src.data(), k);
+        buf[k] = 0;
+    }
+    return SPTRSV_OK;
+}
+
 sptrsv_status_t sptrsv_critical_path(sptrsv_plan_t p, int32_t hop_weight, int64_t *h_cp,
                                      sptrsv_stream_t stream) {
     if (!p || !h_cp) return SPTRSV_ERR_INVALID_ARG;

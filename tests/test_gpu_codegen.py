@@ -113,3 +113,29 @@ def test_generated_and_record_driven_agree_closely():
     P.check()
     # the same terms in a different order (oldest first against storage order)
     assert oracle.relerr(xg, xr) <= 1e-13
+
+
+def test_source_holds_the_matrix_as_constants():
+    """The generated source carries the segment itself: one assignment per
+    row (its folded constant), one FMA per in-segment term with the
+    coefficient as a hexadecimal literal, a function per 32 rows, and no
+    load of any structure array (the only memory reads are the folded
+    constants and earlier unknowns)."""
+    import re
+    from paper_2103_11445_gb300 import binding as B
+    A = mg.chain(200, a=0.5, diag=2.0)     # x_i = (b_i + 0.5 x_{i-1}) / 2
+    P = B.Plan(A.n, A.row_ptr, A.col, A.val)
+    P.transform(**CG)
+    assert P.info()["codegen_segments"] == 1
+    src = P.codegen_source(0)
+    assert src.count("a = s0[") == 200
+    fmas = re.findall(r"a = fma\(([^,]+), (v\[\d+\]|xs\[\d+\]), a\);", src)
+    assert len(fmas) == 199
+    # coefficient -(-0.5) / 2 = 0.25, written exactly
+    assert all(float.fromhex(c) == 0.25 for c, _ in fmas)
+    assert len(re.findall(r"__device__ __noinline__ void g\d+\(", src)) == (200 + 31) // 32
+    assert re.findall(r"x\[(\d+)\] = a;", src) == [str(i) for i in range(200)]
+    for name in ("term", "row_id", "ecol", "eval", "nn["):
+        assert name not in src
+    with pytest.raises(Exception):
+        P.codegen_source(1)                 # one segment only
