@@ -517,6 +517,26 @@ def run_ours(args, world, rank, local):
                                         backoff=info["poll_backoff_ns"])
     except Exception as exc:  # the weights are optional; report why they were not used
         cm_info = dict(error=str(exc)[:200])
+    # the per-segment network's pick (SELECT_SEGMODEL, shipped weights)
+    try:
+        from paper_2103_11445_gb300 import costmodel as cmod
+        if os.path.exists(cmod.SEG_WEIGHTS_BIN):
+            Bd.sptrsv_segmodel_load(cmod.SEG_WEIGHTS_BIN)
+            t0 = time.perf_counter()
+            P.transform(select_mode=Bd.SELECT_SEGMODEL, max_depth=4, solve_mode=Bd.SOLVE_AUTO)
+            tr_ms = (time.perf_counter() - t0) * 1e3
+            ts, _ = timed(5)
+            info = P.info()
+            results["segmodel"] = dict(ms=statistics.median(ts), transform_ms=tr_ms,
+                                       kw=dict(select_mode=Bd.SELECT_SEGMODEL, max_depth=4),
+                                       nlev_new=info["nlev_new"], flops_new=info["flops_new"],
+                                       solve_mode=info["solve_mode"], L=info["lanes_per_row"],
+                                       block=info["block_threads"], grid=info["grid_blocks"],
+                                       cta_run_rows=info["cta_run_rows"],
+                                       backoff=info["poll_backoff_ns"])
+    except Exception as exc:
+        results.pop("segmodel", None)
+        cm_info = dict(cm_info or {}, segmodel_error=str(exc)[:200])
     best = "library_auto"
 
     def tuned(name):

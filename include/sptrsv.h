@@ -38,6 +38,7 @@
 #ifndef SPTRSV_H
 #define SPTRSV_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)
@@ -86,9 +87,20 @@ enum {
     SPTRSV_SELECT_FIXED = 3,      /* merge every `depth`+1 consecutive levels */
     SPTRSV_SELECT_AUTO = 4,       /* measured: times the candidates below on
                                      the plan and keeps the fastest */
-    SPTRSV_SELECT_CRITPATH = 5    /* minimises the critical path of the
+    SPTRSV_SELECT_CRITPATH = 5,   /* minimises the critical path of the
                                      synchronisation-free solve (below) */
+    SPTRSV_SELECT_SEGMODEL = 6    /* per-segment learned cost: a network
+                                     predicts the time each candidate segment
+                                     adds, depths chosen per segment (below;
+                                     without a network: SELECT_CRITPATH) */
 };
+/* SPTRSV_SELECT_SEGMODEL (the matrix-analysis module deciding which levels
+ * to rewrite and how deep, Sec. IV): for every kept level t and depth
+ * d <= min(max_depth, 8) the segment's features (sptrsv_segment_features)
+ * go through the process-wide segment network (sptrsv_segmodel_load), whose
+ * output is the log2 of the time in microseconds the segment's new level
+ * adds to the solve; the segmentation minimising the sum of those times is
+ * found by dynamic programming over the levels, as for SELECT_CRITPATH. */
 /* SPTRSV_SELECT_CRITPATH (the rewriting applied to synchronisation-free
  * execution, Sec. III): a row finishes one hop after the latest of its
  * dependencies plus its own terms, f(i) = hop_weight + terms(i) + max f(dep).
@@ -417,6 +429,35 @@ SPTRSV_API sptrsv_status_t sptrsv_mlp_load(const char *path, sptrsv_mlp_t *out);
 SPTRSV_API sptrsv_status_t sptrsv_costmodel_load(const char *path);
 SPTRSV_API sptrsv_status_t sptrsv_costmodel_save(const char *path);
 SPTRSV_API sptrsv_status_t sptrsv_costmodel_set_default(sptrsv_mlp_t net);
+
+/* The process-wide per-segment network of SPTRSV_SELECT_SEGMODEL (8 input
+ * features, see sptrsv_segment_features), with the same ownership rules as
+ * the cost model's; SPTRSV_ERR_INVALID_ARG for a network of another width. */
+SPTRSV_API sptrsv_status_t sptrsv_segmodel_load(const char *path);
+SPTRSV_API sptrsv_status_t sptrsv_segmodel_set_default(sptrsv_mlp_t net);
+
+/* Features of every candidate segment of the analysed plan: for kept level
+ * t (0 <= t < nlev) and depth d (0 <= d <= d_max <= 16), row t*(d_max+1)+d of
+ * h_feat [nlev*(d_max+1)][8] holds log2(1 + rows), log2(1 + x and b terms),
+ * log2(1 + most terms of a row), terms per row, d, fraction of rows
+ * rewritten, log2 n and log2(nnz/n) of the segment merging levels t..t+d;
+ * h_ok[t*(d_max+1)+d] = 1 where that segment exists within the fill cap
+ * (max_row_fill of the last transform, 1024 before any).  Synchronises
+ * `stream`. */
+SPTRSV_API sptrsv_status_t sptrsv_segment_features(sptrsv_plan_t p, int32_t d_max,
+                                                   float *h_feat, uint8_t *h_ok,
+                                                   sptrsv_stream_t stream);
+
+/* Time of each new level within a solve: `reps` solves of d_b into d_x
+ * (one column), each stamping the completion of every chunk; h_us[g] = the
+ * median over the solves of T(g) - T(g-1), T(g) the latest completion of a
+ * chunk of new levels 0..g (T(-1) the solve's start), so that the times add
+ * up to the solve.  Needs the staged synchronisation-free kernel (FP64, one
+ * column, staging on, no single-CTA tail): SPTRSV_ERR_UNSUPPORTED otherwise.
+ * Synchronises `stream`. */
+SPTRSV_API sptrsv_status_t sptrsv_level_times(sptrsv_plan_t p, const double *d_b, double *d_x,
+                                              int32_t reps, double *h_us,
+                                              sptrsv_stream_t stream);
 
 /* Batched solve (the paper treats one matrix; this serves many independent
  * systems of uneven size at once).  All plans must live on the current

@@ -358,6 +358,31 @@ def costmodel_large_specs(count: int = 80, seed: int = 7000) -> list[dict]:
     return specs
 
 
+def segmodel_specs(count: int = 40, seed: int = 8000) -> list[dict]:
+    """Matrices of the per-segment cost network's data: n log-uniform in
+    [3e4, 2e5], family uniform in {5-point, 7-point, random-banded,
+    thin-tail} (random-banded rows with 5..12 entries, thin tails with a
+    chain of 1-10 % of the rows)."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for m in range(count):
+        n = float(np.exp(rng.uniform(np.log(3e4), np.log(2e5))))
+        fam = ("stencil2d", "stencil3d", "banded", "thin_tail")[int(rng.integers(0, 4))]
+        per_row = int(rng.integers(5, 13))
+        if fam == "stencil2d":
+            side = int(round(n ** 0.5))
+            n_adj = side * side
+        elif fam == "stencil3d":
+            side = int(round(n ** (1.0 / 3.0)))
+            n_adj = side ** 3
+        else:
+            side = 0
+            n_adj = int(round(n))
+        specs.append(dict(index=m, family=fam, n=n_adj, side=side, nrhs=1, per_row=per_row,
+                          chain_frac=float(rng.uniform(0.01, 0.10)), seed=seed + m))
+    return specs
+
+
 def config_matrix(index: int, small: bool = False) -> CSR:
     """The matrix of workload ``index`` (1-based as listed in the module doc).
 

@@ -145,3 +145,28 @@ def segments_cp(segments, table: dict, H: int) -> int:
             m = max(m, table[(t + r, r)])
         tot += H + m
     return tot
+
+
+def select_min_sum(cost: np.ndarray, ok: np.ndarray) -> list[tuple[int, int]]:
+    """The segmentation minimising the sum of per-segment costs (the
+    per-segment learned cost of SELECT_SEGMODEL): cost[t, d] the cost of the
+    segment merging levels t..t+d, ok[t, d] whether it exists.  Dynamic
+    programming from the last level down, best[t] = min over d of
+    cost[t, d] + best[t + d + 1], a depth stopping at its first missing
+    segment, ties to the smaller d."""
+    nlev, D = cost.shape
+    best = [float("inf")] * (nlev + 1)
+    choice = [0] * (nlev + 1)
+    best[nlev] = 0.0
+    for t in range(nlev - 1, -1, -1):
+        for d in range(D):
+            if t + d >= nlev or not ok[t, d]:
+                break
+            c = float(cost[t, d]) + best[t + d + 1]
+            if c < best[t]:
+                best[t], choice[t] = c, d
+    segs, t = [], 0
+    while t < nlev:
+        segs.append((t, choice[t]))
+        t += choice[t] + 1
+    return segs

@@ -26,6 +26,8 @@ STATUS_NAMES = {
 }
 SELECT_NONE, SELECT_HEURISTIC, SELECT_COSTMODEL, SELECT_FIXED, SELECT_AUTO, SELECT_CRITPATH = \
     0, 1, 2, 3, 4, 5
+SELECT_SEGMODEL = 6
+SEG_FEATURES = 8
 SOLVE_AUTO, SOLVE_BARRIER, SOLVE_SYNCFREE = 0, 1, 2
 F64, F32_IR = 0, 1
 OP_LOWER, OP_UPPER, OP_LOWER_TRANS, OP_UPPER_TRANS = 0, 1, 2, 3
@@ -120,6 +122,10 @@ _SIGS = {
     "sptrsv_costmodel_load": (c_int32, [ctypes.c_char_p]),
     "sptrsv_costmodel_save": (c_int32, [ctypes.c_char_p]),
     "sptrsv_costmodel_set_default": (c_int32, [c_void_p]),
+    "sptrsv_segmodel_load": (c_int32, [c_char_p]),
+    "sptrsv_segmodel_set_default": (c_int32, [c_void_p]),
+    "sptrsv_segment_features": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "sptrsv_level_times": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "sptrsv_batch_create": (c_int32, [c_void_p, c_int32, POINTER(c_void_p)]),
     "sptrsv_batch_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sptrsv_batch_check": (c_int32, [c_void_p, c_void_p]),
@@ -400,6 +406,34 @@ def sptrsv_costmodel_set_default(mlp: int) -> None:
     _check(load().sptrsv_costmodel_set_default(mlp), "sptrsv_costmodel_set_default")
 
 
+def sptrsv_segmodel_load(path: str) -> None:
+    _check(load().sptrsv_segmodel_load(os.fsencode(path)), "sptrsv_segmodel_load")
+
+
+def sptrsv_segmodel_set_default(mlp: int) -> None:
+    _check(load().sptrsv_segmodel_set_default(mlp), "sptrsv_segmodel_set_default")
+
+
+def sptrsv_segment_features(plan: int, nlev: int, d_max: int, stream: int = 0):
+    """(features [nlev, d_max + 1, SEG_FEATURES] float32, ok [nlev, d_max + 1] bool)."""
+    import numpy as np
+    f = np.zeros((nlev, d_max + 1, SEG_FEATURES), np.float32)
+    ok = np.zeros((nlev, d_max + 1), np.uint8)
+    _check(load().sptrsv_segment_features(plan, d_max, f.ctypes.data, ok.ctypes.data, stream),
+           "sptrsv_segment_features")
+    return f, ok.astype(bool)
+
+
+def sptrsv_level_times(plan: int, d_b: int, d_x: int, nlev_new: int, reps: int = 3,
+                       stream: int = 0):
+    """Microseconds each new level adds to a solve (median over reps)."""
+    import numpy as np
+    us = np.zeros(nlev_new, np.float64)
+    _check(load().sptrsv_level_times(plan, d_b, d_x, reps, us.ctypes.data, stream),
+           "sptrsv_level_times")
+    return us
+
+
 def sptrsv_batch_create(plans) -> int:
     arr = (c_void_p * len(plans))(*plans)
     out = c_void_p()
@@ -556,6 +590,17 @@ class Plan:
 
     def segments(self):
         return sptrsv_get_segments(self._handle, self.info()["nlev_new"])
+
+    def segment_features(self, d_max: int = 4):
+        """Features of every candidate segment (see sptrsv_segment_features)."""
+        return sptrsv_segment_features(self._handle, self.info()["nlev"], d_max)
+
+    def level_times(self, b, reps: int = 3):
+        """Microseconds each new level adds to a solve of b (one column)."""
+        import torch
+        x = torch.empty_like(b)
+        return sptrsv_level_times(self._handle, b.data_ptr(), x.data_ptr(),
+                                  self.info()["nlev_new"], reps)
 
     def codegen_source(self, seg: int = 0) -> str:
         """Source of the kernel generated for tail segment seg."""

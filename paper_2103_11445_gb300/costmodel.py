@@ -21,6 +21,7 @@ flushed before each).
 from __future__ import annotations
 
 import argparse
+import json
 import os
 import statistics
 import sys
@@ -244,6 +245,94 @@ def regret(model: CostModel, X, y, group, h_times):
         matrices=int(r.shape[0]))
 
 
+# --- per-segment network (SELECT_SEGMODEL) --------------------------------------
+
+SEG_WEIGHTS_BIN = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                               "segmodel_weights.bin")
+SEG_HIDDEN = 32
+SEG_DMAX = 4
+# segmentations timed per matrix: their new levels are the training rows
+SEG_SELECTIONS = (
+    ("plain", dict(select_mode=B.SELECT_NONE)),
+    ("d1", dict(select_mode=B.SELECT_FIXED, depth=1)),
+    ("d2", dict(select_mode=B.SELECT_FIXED, depth=2)),
+    ("cp16", dict(select_mode=B.SELECT_CRITPATH, hop_weight=16, max_depth=4)),
+    ("thin8", dict(select_mode=B.SELECT_HEURISTIC, thin_rows=THIN_ROWS, max_depth=8,
+                   flop_budget=THIN_BUDGET)),
+)
+# the launch every segmentation is timed with (the staged kernel)
+SEG_LAUNCH = dict(solve_mode=B.SOLVE_SYNCFREE, lanes_per_row=2, block_threads=128,
+                  grid_blocks=0, tail_rows=-1, cta_run_rows=-1)
+
+
+def seg_collect(specs, reps: int = 3, log=None):
+    """Rows: the features of each new level of each timed segmentation and
+    the log2 of the microseconds that level added (sptrsv_level_times);
+    plus each plan's total time (us) per matrix and selection."""
+    import torch
+    import matgen as mg
+    dev = torch.device("cuda", torch.cuda.current_device())
+    X, y, group, totals = [], [], [], []
+    for k, sp in enumerate(specs):
+        A = mg.make_from_spec(sp)
+        P = B.Plan(A.n, A.row_ptr, A.col, A.val)
+        feat, ok = P.segment_features(SEG_DMAX)
+        b = torch.ones(A.n, dtype=torch.float64, device=dev)
+        tot = {}
+        for name, kw in SEG_SELECTIONS:
+            P.transform(**kw, **SEG_LAUNCH)
+            first, depth = P.segments()
+            us = P.level_times(b, reps)
+            tot[name] = float(us.sum())
+            for g, (t, d) in enumerate(zip(first, depth)):
+                if d <= SEG_DMAX and ok[t, d]:
+                    X.append(feat[t, d])
+                    y.append(np.log2(max(float(us[g]), 0.02)))
+                    group.append(k)
+        totals.append(tot)
+        P.close()
+        if log:
+            log(f"{k + 1}/{len(specs)} {sp['family']} n={A.n}: " +
+                " ".join(f"{n} {v / 1e3:.3f}" for n, v in tot.items()))
+    return (np.asarray(X, np.float32), np.asarray(y, np.float32), np.asarray(group, np.int32),
+            totals)
+
+
+def seg_evaluate(model: "CostModel", specs, reps: int = 7, log=None) -> dict:
+    """On each matrix: the solve time of the network's segmentation
+    (SELECT_SEGMODEL) against every timed segmentation (the exhaustive
+    search over them: plain, depths 1 and 2, the critical-path selection, H
+    on thin levels), one launch."""
+    import matgen as mg
+    B.sptrsv_segmodel_set_default(model.handle)
+    rows = []
+    try:
+        for sp in specs:
+            A = mg.make_from_spec(sp)
+            P = B.Plan(A.n, A.row_ptr, A.col, A.val)
+            t = {}
+            for name, kw in SEG_SELECTIONS:
+                P.transform(**kw, **SEG_LAUNCH)
+                t[name] = time_solves(P, A.n, reps)
+            P.transform(select_mode=B.SELECT_SEGMODEL, max_depth=SEG_DMAX, **SEG_LAUNCH)
+            t["segmodel"] = time_solves(P, A.n, reps)
+            P.close()
+            best = min(v for k, v in t.items() if k != "segmodel")
+            rows.append((t["segmodel"] / best, t["thin8"] / t["segmodel"],
+                         t["plain"] / t["segmodel"], t["cp16"] / t["segmodel"]))
+            if log:
+                log(f"{sp['family']} n={A.n}: segmodel {t['segmodel']:.1f} us, best "
+                    f"{best:.1f} us, regret {rows[-1][0]:.3f}")
+    finally:
+        B.sptrsv_segmodel_set_default(0)
+    r = np.asarray(rows)
+    geo = lambda a: float(np.exp(np.mean(np.log(a))))
+    return dict(matrices=len(rows), geo_regret=geo(r[:, 0]), mean_regret=float(r[:, 0].mean()),
+                within_5pct=float(np.mean(r[:, 0] <= 1.05)),
+                geo_speedup_vs_thin_levels_h=geo(r[:, 1]), geo_speedup_vs_plain=geo(r[:, 2]),
+                geo_speedup_vs_critpath=geo(r[:, 3]))
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(prog="costmodel")
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -263,6 +352,14 @@ def main(argv=None) -> int:
     t.add_argument("--lr", type=float, default=3e-3)
     t.add_argument("--extra", default=None,
                    help="additional training-only data (e.g. the larger matrices)")
+    g = sub.add_parser("segmodel", help="collect, train and evaluate the per-segment network")
+    g.add_argument("--count", type=int, default=40)
+    g.add_argument("--seed", type=int, default=8000)
+    g.add_argument("--train-frac", type=float, default=0.75)
+    g.add_argument("--epochs", type=int, default=3000)
+    g.add_argument("--lr", type=float, default=3e-3)
+    g.add_argument("--data-out", default=None)
+    g.add_argument("--out", default=SEG_WEIGHTS_BIN)
     x = sub.add_parser("export", help="write weights as the library's network file")
     x.add_argument("--weights", default=WEIGHTS)
     x.add_argument("--out", default=WEIGHTS_BIN)
@@ -278,6 +375,25 @@ def main(argv=None) -> int:
         return 0
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import matgen as mg
+    if args.cmd == "segmodel":
+        specs = mg.segmodel_specs(args.count, seed=args.seed)
+        cut = int(round(len(specs) * args.train_frac))
+        t0 = time.time()
+        X, y, g, totals = seg_collect(specs[:cut], log=lambda s: print(s, flush=True))
+        print(f"collected {len(y)} level rows from {cut} matrices in {time.time() - t0:.1f} s")
+        if args.data_out:
+            np.savez(args.data_out, X=X, y=y, group=g,
+                     totals=np.array([str(t) for t in totals]),
+                     specs=np.array([str(s) for s in specs]))
+        m = CostModel(n_in=B.SEG_FEATURES, hidden=SEG_HIDDEN)
+        hist = m.fit(X, y, epochs=args.epochs, lr=args.lr, log_every=500)
+        for e, l in hist:
+            print(f"epoch {e}: train mse {l:.4f}")
+        res = seg_evaluate(m, specs[cut:], log=lambda s: print(s, flush=True))
+        res["train_mse_log2"] = float(hist[-1][1])
+        print(json.dumps(res))
+        m.save(args.out)
+        return 0
     if args.cmd == "collect":
         if args.large:
             specs = mg.costmodel_large_specs(args.large)

@@ -20,6 +20,7 @@ using namespace sptrsv;
 namespace sptrsv {
 // mlp.cu: normalise h_feat [count][16] and run the network, h_pred[count]
 sptrsv_mlp_t default_costmodel();   // mlp.cu: the process-wide network, or null
+sptrsv_mlp_t default_segmodel();    // mlp.cu: the per-segment network, or null
 sptrsv_status_t costmodel_predict(sptrsv_mlp_t net, const float *h_feat, int count,
                                   float *h_pred, cudaStream_t s);
 }
@@ -264,6 +265,115 @@ sptrsv_status_t critpath_segments(sptrsv_plan_t p, int64_t hop, int32_t d_max, c
     return SPTRSV_OK;
 }
 
+// Features of every candidate segment (t, d <= d_max) -- the analysis of
+// the levels it merges and the lift counts of its rewritten rows (the
+// matrix-analysis module's per-level view, Sec. IV), as the per-segment cost
+// network of SELECT_SEGMODEL reads them:
+//   0 log2(1 + rows), 1 log2(1 + x and b terms), 2 log2(1 + most terms of a
+//   row), 3 terms per row, 4 d, 5 fraction of rows rewritten, 6 log2 n,
+//   7 log2(nnz / n).
+// ok[t * (d_max + 1) + d] = 0 where t + d runs past the last level or a
+// lifted row would exceed the fill cap.
+sptrsv_status_t segment_table(sptrsv_plan_t p, int32_t d_max, cudaStream_t s,
+                              std::vector<float> &feat, std::vector<uint8_t> &ok) {
+    const int32_t nlev = p->nlev, D = d_max + 1;
+    feat.assign((size_t)nlev * D * kSegFeatures, 0.0f);
+    ok.assign((size_t)nlev * D, 0);
+    if (nlev == 0) return SPTRSV_OK;
+    std::vector<int32_t> lm0(nlev, 0);
+    std::vector<unsigned long long> acc((size_t)nlev * 11, 0);
+    {
+        DevArr<int32_t> lm;
+        DevArr<unsigned long long> dacc;
+        CK(lm.alloc(nlev));
+        CK(dacc.alloc((size_t)nlev * 11));
+        CK(cudaMemsetAsync(lm.p, 0, nlev * sizeof(int32_t), s));
+        CK(cudaMemsetAsync(dacc.p, 0, (size_t)nlev * 11 * sizeof(unsigned long long), s));
+        CK(launch_level_max(p->n, p->level.p, p->offdeg.p, lm.p, s));
+        CK(launch_level_counts(p->n, p->row_ptr.p, p->col.p, p->level.p, dacc.p, s));
+        CK(cudaMemcpyAsync(lm0.data(), lm.p, nlev * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(acc.data(), dacc.p, acc.size() * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    FillQuery fo{p, s, p->prm.max_row_fill, {}};
+    std::vector<std::pair<int32_t, int32_t>> qs;
+    for (int32_t l = 1; l < nlev; ++l)
+        for (int32_t r = 1; r <= std::min(d_max, l); ++r) qs.emplace_back(l, r);
+    CKS(fo.run(qs));
+    const float ln = std::log2((float)std::max<int32_t>(p->n, 1));
+    const float ld = std::log2((float)std::max<int64_t>(p->nnz, 1) / std::max<int32_t>(p->n, 1));
+    for (int32_t t = 0; t < nlev; ++t) {
+        double rows = 0, terms = 0, maxt = 0, rew = 0;
+        for (int32_t d = 0; d <= d_max && t + d < nlev; ++d) {
+            const int32_t l = t + d;
+            const double rl = (double)acc[(size_t)l * 11 + 0];
+            if (d == 0) {
+                terms += (double)acc[(size_t)l * 11 + 1];
+                maxt = lm0[t];
+            } else {
+                const int64_t add = fo.cache[{l, d}];
+                if (add < 0) break;   // deeper merges lift this level too
+                terms += (double)acc[(size_t)l * 11 + 1] + 0.5 * (double)add;
+                maxt = std::max<double>(maxt, fo.maxlen[{l, d}]);
+                rew += rl;
+            }
+            rows += rl;
+            float *f = &feat[((size_t)t * D + d) * kSegFeatures];
+            f[0] = (float)std::log2(1.0 + rows);
+            f[1] = (float)std::log2(1.0 + terms);
+            f[2] = (float)std::log2(1.0 + maxt);
+            f[3] = (float)(terms / std::max(rows, 1.0));
+            f[4] = (float)d;
+            f[5] = (float)(rew / std::max(rows, 1.0));
+            f[6] = ln;
+            f[7] = ld;
+            ok[(size_t)t * D + d] = 1;
+        }
+    }
+    return SPTRSV_OK;
+}
+
+// SELECT_SEGMODEL: the network predicts the log2 time (us) each candidate
+// segment adds to the solve; the segmentation minimising the sum, by
+// dynamic programming over the levels as in SELECT_CRITPATH (ties to the
+// smaller depth).
+sptrsv_status_t segmodel_segments(sptrsv_plan_t p, sptrsv_mlp_t net, int32_t d_max,
+                                  cudaStream_t s, std::vector<std::pair<int32_t, int32_t>> *out) {
+    const int32_t nlev = p->nlev, D = d_max + 1;
+    std::vector<float> feat;
+    std::vector<uint8_t> ok;
+    CKS(segment_table(p, d_max, s, feat, ok));
+    std::vector<float> pred((size_t)nlev * D, 0.0f);
+    // the feasible rows only, in one batch
+    std::vector<float> fx;
+    std::vector<int64_t> at;
+    for (size_t i = 0; i < ok.size(); ++i)
+        if (ok[i]) {
+            fx.insert(fx.end(), feat.begin() + i * kSegFeatures,
+                      feat.begin() + (i + 1) * kSegFeatures);
+            at.push_back((int64_t)i);
+        }
+    std::vector<float> px(at.size());
+    if (!at.empty()) CKS(costmodel_predict(net, fx.data(), (int)at.size(), px.data(), s));
+    for (size_t k = 0; k < at.size(); ++k) pred[at[k]] = px[k];
+    std::vector<double> best(nlev + 1, INFINITY);
+    std::vector<int32_t> choice(nlev + 1, 0);
+    best[nlev] = 0.0;
+    for (int32_t t = nlev - 1; t >= 0; --t)
+        for (int32_t d = 0; d <= d_max && t + d < nlev; ++d) {
+            if (!ok[(size_t)t * D + d]) break;
+            const double c = std::exp2((double)pred[(size_t)t * D + d]) + best[t + d + 1];
+            if (c < best[t]) {
+                best[t] = c;
+                choice[t] = d;
+            }
+        }
+    out->clear();
+    for (int32_t t = 0; t < nlev; t += choice[t] + 1) out->emplace_back(t, choice[t]);
+    return SPTRSV_OK;
+}
+
 // Candidate rewrite depths the cost model chooses from (0 = plain levels).
 // Candidates of SELECT_COSTMODEL.  A code c < kThinOnly merges every c+1
 // levels (c = 0: the plain level sets); c = kThinOnly + d rewrites only the
@@ -362,7 +472,18 @@ sptrsv_status_t choose_segments(sptrsv_plan_t p, cudaStream_t s) {
             d_max = kCostDepths[best];
             rho = INFINITY;
         }
-    } else if (prm.select_mode == SPTRSV_SELECT_CRITPATH) {
+    } else if (prm.select_mode == SPTRSV_SELECT_SEGMODEL && default_segmodel()) {
+        std::vector<std::pair<int32_t, int32_t>> segs;
+        CKS(segmodel_segments(p, default_segmodel(), std::min(std::max(prm.max_depth, 0), 8), s,
+                              &segs));
+        for (auto &sg : segs) {
+            p->seg_first.push_back(sg.first);
+            p->seg_depth.push_back(sg.second);
+        }
+        return SPTRSV_OK;
+    } else if (prm.select_mode == SPTRSV_SELECT_CRITPATH ||
+               prm.select_mode == SPTRSV_SELECT_SEGMODEL) {
+        // (SELECT_SEGMODEL without a network: the critical-path selection)
         std::vector<std::pair<int32_t, int32_t>> segs;
         CKS(critpath_segments(p, prm.hop_weight > 0 ? prm.hop_weight : 16, prm.max_depth, s,
                               &segs));
@@ -1589,7 +1710,7 @@ sptrsv_status_t sptrsv_transform(sptrsv_plan_t p, const sptrsv_transform_params_
     if (!p || !prm) return SPTRSV_ERR_INVALID_ARG;
     if (p->latched != SPTRSV_OK) return SPTRSV_ERR_BAD_STATE;
     if (prm->select_mode == SPTRSV_SELECT_AUTO) return select_auto(p, prm, stream);
-    if (prm->select_mode < 0 || prm->select_mode > 5 || prm->solve_mode < 0 ||
+    if (prm->select_mode < 0 || prm->select_mode > 6 || prm->solve_mode < 0 ||
         prm->solve_mode > 2 || (prm->precision != SPTRSV_F64 && prm->precision != SPTRSV_F32_IR))
         return SPTRSV_ERR_INVALID_ARG;
     if (prm->lanes_per_row != 0 && prm->lanes_per_row != 1 && prm->lanes_per_row != 2 &&
@@ -1846,6 +1967,60 @@ sptrsv_status_t sptrsv_level_features(sptrsv_plan_t p, int32_t lifts, float *h_f
         for (int k = 0; k < 11; ++k) f[k] = (float)acc[(size_t)l * 11 + k];
         for (int r = 1; r <= lifts; ++r)
             f[10 + r] = r <= l ? (float)fo.cache[{l, r}] : 0.f;   // -1: over the fill cap
+    }
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_segment_features(sptrsv_plan_t p, int32_t d_max, float *h_feat,
+                                        uint8_t *h_ok, sptrsv_stream_t stream) {
+    if (!p || !h_feat || !h_ok || d_max < 0 || d_max > 16) return SPTRSV_ERR_INVALID_ARG;
+    if (p->latched != SPTRSV_OK) return SPTRSV_ERR_BAD_STATE;
+    std::vector<float> feat;
+    std::vector<uint8_t> ok;
+    CKS(segment_table(p, d_max, (cudaStream_t)stream, feat, ok));
+    std::memcpy(h_feat, feat.data(), feat.size() * sizeof(float));
+    std::memcpy(h_ok, ok.data(), ok.size());
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_level_times(sptrsv_plan_t p, const double *d_b, double *d_x,
+                                   int32_t reps, double *h_us, sptrsv_stream_t stream) {
+    if (!p || !d_b || !d_x || !h_us || reps < 1) return SPTRSV_ERR_INVALID_ARG;
+    if (p->latched != SPTRSV_OK) return SPTRSV_ERR_BAD_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int32_t nl = p->s64.nlev;
+    const int stz = stage_width(p, p->s64);
+    if (p->prm.precision == SPTRSV_F32_IR || !p->cfg.syncfree || stz <= 0 ||
+        tail_active(p, 1) || !p->s64.built || nl <= 0)
+        return SPTRSV_ERR_UNSUPPORTED;
+    SolveData<double> sd = p->s64.view();
+    sd.backoff_ns = p->cfg.backoff_ns;
+    sd.stage_z = stz;
+    if (!p->cfg.sched_lm) sd.sched = nullptr;
+    DevArr<unsigned long long> ns;
+    CK(ns.alloc((size_t)nl + 1));
+    sd.level_ns = ns.p;
+    LaunchCfg lc{p->cfg.block_threads, grid_for(p, 1, false)};
+    if (lc.grid <= 0) return SPTRSV_ERR_CUDA;
+    std::vector<std::vector<double>> inc(nl);
+    std::vector<unsigned long long> h((size_t)nl + 1);
+    for (int32_t r = 0; r < reps; ++r) {
+        CK(cudaMemsetAsync(ns.p, 0, ((size_t)nl + 1) * sizeof(unsigned long long), s));
+        CK(launch_solve<double>(sd, d_b, d_x, p->n, 1, 1, true, lc, p->status.p, timeout_ns(p),
+                                false, s));
+        CK(cudaMemcpyAsync(h.data(), ns.p, h.size() * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+        CKS(sync_status(p, s));
+        unsigned long long prev = h[0];
+        for (int32_t g = 0; g < nl; ++g) {
+            const unsigned long long t = std::max(prev, h[1 + g]);
+            inc[g].push_back((double)(t - prev) * 1e-3);
+            prev = t;
+        }
+    }
+    for (int32_t g = 0; g < nl; ++g) {
+        std::sort(inc[g].begin(), inc[g].end());
+        h_us[g] = inc[g][inc[g].size() / 2];
     }
     return SPTRSV_OK;
 }

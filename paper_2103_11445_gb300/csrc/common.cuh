@@ -20,6 +20,9 @@ constexpr int32_t PAD_COL = INT32_MIN;
 // (not divided by its diagonal); the record's count field holds it above
 // the count (bits 0-7) and the mask of terms read from x (bits 8-23).
 constexpr int32_t kTailUnscaled = 1 << 30;
+// Features of one candidate segment (kept level t, depth d) for the
+// per-segment cost network of SELECT_SEGMODEL.
+constexpr int kSegFeatures = 8;
 
 // Device status block of a plan (zeroed at creation):
 //  [0] error code (first one wins), [1] row or index involved,

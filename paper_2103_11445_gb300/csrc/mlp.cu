@@ -219,21 +219,21 @@ cudaError_t backward(sptrsv_mlp_t net, const float *X, const float *tgt, int N, 
 namespace sptrsv {
 // Normalises h_feat [count][F] with the network's stored statistics and
 // returns the predictions in h_pred (synchronises the stream).
+// Predictions of the network for `count` raw feature rows (host): the rows
+// are standardised on the device by the same kernel the training uses
+// (sptrsv_mlp_normalize), so that a selection sees exactly the network's
+// training-time arithmetic.
 sptrsv_status_t costmodel_predict(sptrsv_mlp_t net, const float *h_feat, int count,
                                   float *h_pred, cudaStream_t s) {
     if (!net || count <= 0) return SPTRSV_ERR_INVALID_ARG;
     const int F = net->F;
-    std::vector<float> x((size_t)count * F);
-    for (int i = 0; i < count; ++i)
-        for (int f = 0; f < F; ++f) {
-            const float m = net->has_norm ? net->feat_mean[f] : 0.f;
-            const float sd = net->has_norm ? net->feat_std[f] : 1.f;
-            x[(size_t)i * F + f] = (h_feat[(size_t)i * F + f] - m) / sd;
-        }
-    DevArr<float> dx, dy;
-    if (dx.alloc(x.size()) || dy.alloc(count)) return SPTRSV_ERR_OOM;
-    if (cudaMemcpyAsync(dx.p, x.data(), x.size() * sizeof(float), cudaMemcpyHostToDevice, s))
+    DevArr<float> dx;
+    if (dx.alloc((size_t)count * F)) return SPTRSV_ERR_OOM;
+    if (cudaMemcpyAsync(dx.p, h_feat, (size_t)count * F * sizeof(float), cudaMemcpyHostToDevice,
+                        s))
         return SPTRSV_ERR_CUDA;
+    const sptrsv_status_t st = sptrsv_mlp_normalize(net, dx.p, count, dx.p, s);
+    if (st != SPTRSV_OK) return st;
     if (ensure_cap(net, count) != SPTRSV_OK) return SPTRSV_ERR_OOM;
     if (forward(net, dx.p, count, s) != cudaSuccess) return SPTRSV_ERR_CUDA;
     if (cudaMemcpyAsync(h_pred, net->y.p, count * sizeof(float), cudaMemcpyDeviceToHost, s) ||
@@ -241,12 +241,30 @@ sptrsv_status_t costmodel_predict(sptrsv_mlp_t net, const float *h_feat, int cou
         return SPTRSV_ERR_CUDA;
     return SPTRSV_OK;
 }
-// The process-wide default network of SELECT_COSTMODEL (sptrsv_costmodel_load).
+// The process-wide default networks of SELECT_COSTMODEL
+// (sptrsv_costmodel_load) and SELECT_SEGMODEL (sptrsv_segmodel_load); a
+// network loaded from a file is owned by the library, one handed over by
+// set_default stays the caller's.
 std::mutex g_default_mu;
 sptrsv_mlp_t g_default_net = nullptr;
+bool g_default_owned = false;
+sptrsv_mlp_t g_segment_net = nullptr;
+bool g_segment_owned = false;
 sptrsv_mlp_t default_costmodel() {
     std::lock_guard<std::mutex> lock(g_default_mu);
     return g_default_net;
+}
+sptrsv_mlp_t default_segmodel() {
+    std::lock_guard<std::mutex> lock(g_default_mu);
+    return g_segment_net;
+}
+// Replaces a default network; returns the old one if the library owned it.
+sptrsv_mlp_t swap_default(sptrsv_mlp_t &slot, bool &owned, sptrsv_mlp_t net, bool own) {
+    std::lock_guard<std::mutex> lock(g_default_mu);
+    sptrsv_mlp_t old = owned && slot != net ? slot : nullptr;
+    slot = net;
+    owned = net && own;
+    return old;
 }
 }  // namespace sptrsv
 
@@ -353,7 +371,14 @@ SPTRSV_API void sptrsv_mlp_destroy(sptrsv_mlp_t net) {
     if (!net) return;
     {
         std::lock_guard<std::mutex> lock(sptrsv::g_default_mu);
-        if (sptrsv::g_default_net == net) sptrsv::g_default_net = nullptr;
+        if (sptrsv::g_default_net == net) {
+            sptrsv::g_default_net = nullptr;
+            sptrsv::g_default_owned = false;
+        }
+        if (sptrsv::g_segment_net == net) {
+            sptrsv::g_segment_net = nullptr;
+            sptrsv::g_segment_owned = false;
+        }
     }
     cudaDeviceSynchronize();
     delete net;
@@ -464,12 +489,8 @@ SPTRSV_API sptrsv_status_t sptrsv_costmodel_load(const char *path) {
     sptrsv_mlp_t net = nullptr;
     sptrsv_status_t st = sptrsv_mlp_load(path, &net);
     if (st != SPTRSV_OK) return st;
-    sptrsv_mlp_t old;
-    {
-        std::lock_guard<std::mutex> lock(sptrsv::g_default_mu);
-        old = sptrsv::g_default_net;
-        sptrsv::g_default_net = net;
-    }
+    sptrsv_mlp_t old =
+        sptrsv::swap_default(sptrsv::g_default_net, sptrsv::g_default_owned, net, true);
     if (old) {
         cudaDeviceSynchronize();
         delete old;
@@ -484,8 +505,40 @@ SPTRSV_API sptrsv_status_t sptrsv_costmodel_save(const char *path) {
 }
 
 SPTRSV_API sptrsv_status_t sptrsv_costmodel_set_default(sptrsv_mlp_t net) {
-    std::lock_guard<std::mutex> lock(sptrsv::g_default_mu);
-    sptrsv::g_default_net = net;
+    sptrsv_mlp_t old =
+        sptrsv::swap_default(sptrsv::g_default_net, sptrsv::g_default_owned, net, false);
+    if (old) {
+        cudaDeviceSynchronize();
+        delete old;
+    }
+    return SPTRSV_OK;
+}
+
+SPTRSV_API sptrsv_status_t sptrsv_segmodel_load(const char *path) {
+    sptrsv_mlp_t net = nullptr;
+    sptrsv_status_t st = sptrsv_mlp_load(path, &net);
+    if (st != SPTRSV_OK) return st;
+    if (net->F != sptrsv::kSegFeatures) {
+        delete net;
+        return SPTRSV_ERR_INVALID_ARG;
+    }
+    sptrsv_mlp_t old =
+        sptrsv::swap_default(sptrsv::g_segment_net, sptrsv::g_segment_owned, net, true);
+    if (old) {
+        cudaDeviceSynchronize();
+        delete old;
+    }
+    return SPTRSV_OK;
+}
+
+SPTRSV_API sptrsv_status_t sptrsv_segmodel_set_default(sptrsv_mlp_t net) {
+    if (net && net->F != sptrsv::kSegFeatures) return SPTRSV_ERR_INVALID_ARG;
+    sptrsv_mlp_t old =
+        sptrsv::swap_default(sptrsv::g_segment_net, sptrsv::g_segment_owned, net, false);
+    if (old) {
+        cudaDeviceSynchronize();
+        delete old;
+    }
     return SPTRSV_OK;
 }
 

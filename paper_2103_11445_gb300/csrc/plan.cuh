@@ -90,6 +90,8 @@ struct SolveStruct {
         v.sched_nw = sched.p ? sched_nw : 0;
         v.blob = blob_valid ? blob.p : nullptr;
         v.bofs = blob_valid ? bofs.p : nullptr;
+        v.chunk_level = chunk_level.p;
+        v.level_ns = nullptr;   // set by a level-timed solve
         return v;
     }
 };

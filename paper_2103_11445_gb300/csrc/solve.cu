@@ -981,6 +981,7 @@ solve_staged_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, DevStatu
             *reinterpret_cast<typename Bits<T>::U *>(out + (int64_t)row * ld) = Sentinel<T>::bits;
     }
     const bool ok = grid_barrier(st, gridDim.x, timeout_ns, -5);
+    if (sd.level_ns && blockIdx.x == 0 && threadIdx.x == 0) sd.level_ns[0] = globaltimer_ns();
     // Each warp solves its chunks in order (the progress argument of
     // solve_syncfree_kernel holds for both schedules; the copies a chunk
     // waits for depend on nothing but the structure).
@@ -1007,6 +1008,9 @@ solve_staged_kernel(SolveData<T> sd, const double *rhs, T *out, int ld, DevStatu
             bail = chunk_one<T, L, true>(sd, c, out, cx);
         }
         if (bail) break;
+        if (sd.level_ns && (threadIdx.x & 31) == 0)
+            atomicMax(sd.level_ns + 1 + __ldg(sd.chunk_level + c),
+                      (unsigned long long)globaltimer_ns());
         __syncwarp();
         blob_range(sd, cn3, u2a, u2b);
         c = cn1;

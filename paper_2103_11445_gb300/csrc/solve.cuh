@@ -50,6 +50,12 @@ struct SolveData {
     // 16-byte units [bofs[c], bofs[c + 1]) of blob.
     const uint4 *blob;
     const int64_t *bofs;
+    // Level-timed solve (staged kernel only): level_ns[0] = the start of the
+    // solve, level_ns[1 + g] = the latest completion time of a chunk of new
+    // level g (%globaltimer); null: no stamps.  chunk_level[c] = new level
+    // of chunk c.
+    const int32_t *chunk_level;
+    unsigned long long *level_ns;
 };
 
 // One chunk as one contiguous run of 16-byte units: unit 0 the chunk

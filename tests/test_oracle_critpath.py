@@ -126,3 +126,37 @@ def test_large_hop_weight_merges_and_small_one_keeps_levels():
     assert len(deep) == -(-nlev // 3)
     flat = cpo.select_critpath(nlev, table, 0, 2)
     assert all(d == 0 for _, d in flat)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_min_sum_segmentation_equals_brute_force(seed):
+    """select_min_sum against every composition of a few levels into
+    segments of 1..D levels, with random costs and random missing segments
+    (a missing segment also rules out the deeper ones from its level)."""
+    rng = np.random.default_rng(seed)
+    nlev, D = 9, 4
+    cost = rng.uniform(0.1, 3.0, (nlev, D))
+    ok = rng.random((nlev, D)) > 0.2
+    ok[:, 0] = True
+    for t in range(nlev):           # missing at d: missing deeper too
+        for d in range(1, D):
+            ok[t, d] = ok[t, d] and ok[t, d - 1] and t + d < nlev
+    best = None
+    for parts in compositions(nlev, D - 1):
+        segs = segs_of(parts)
+        if all(ok[t, d] for t, d in segs):
+            v = sum(cost[t, d] for t, d in segs)
+            best = v if best is None else min(best, v)
+    segs = cpo.select_min_sum(cost, ok)
+    assert sum(d + 1 for _, d in segs) == nlev
+    assert np.isclose(sum(cost[t, d] for t, d in segs), best)
+
+
+def test_min_sum_ties_go_to_the_smaller_depth():
+    cost = np.ones((3, 3))
+    cost[0, 2] = 1.0                 # one segment of 3 levels costs 1 = one level
+    ok = np.ones((3, 3), bool)
+    ok[1, 2] = ok[2, 1] = ok[2, 2] = False
+    assert cpo.select_min_sum(cost, ok) == [(0, 2)]
+    cost[0, 2] = 3.0                 # now (0..1)(2) and (0)(1..2) tie at 2:
+    assert cpo.select_min_sum(cost, ok) == [(0, 0), (1, 1)]   # level 0 keeps d = 0
