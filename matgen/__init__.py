@@ -383,6 +383,23 @@ def segmodel_specs(count: int = 40, seed: int = 8000) -> list[dict]:
     return specs
 
 
+def segmodel_large_specs() -> list[dict]:
+    """Large training-only matrices of the per-segment network: 7-point
+    stencils of side 90, 110 and 120 (not the benchmark's 128),
+    5-point of side 800 and 1200, thin tails of 5e5 and 1e6 rows, a
+    random-banded matrix of 6e5 rows."""
+    specs = []
+    for k, (fam, size) in enumerate((("stencil3d", 90), ("stencil3d", 110), ("stencil3d", 120),
+                                     ("stencil2d", 800), ("stencil2d", 1200),
+                                     ("thin_tail", 500_000), ("thin_tail", 1_000_000),
+                                     ("banded", 600_000))):
+        side = size if fam.startswith("stencil") else 0
+        n = side ** 3 if fam == "stencil3d" else side ** 2 if fam == "stencil2d" else size
+        specs.append(dict(index=k, family=fam, n=n, side=side, nrhs=1, per_row=8,
+                          chain_frac=0.05, seed=8500 + k))
+    return specs
+
+
 def config_matrix(index: int, small: bool = False) -> CSR:
     """The matrix of workload ``index`` (1-based as listed in the module doc).
 

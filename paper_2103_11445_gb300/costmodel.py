@@ -360,6 +360,8 @@ def main(argv=None) -> int:
     g.add_argument("--lr", type=float, default=3e-3)
     g.add_argument("--data-out", default=None)
     g.add_argument("--out", default=SEG_WEIGHTS_BIN)
+    g.add_argument("--large", action="store_true",
+                   help="add eight large training-only matrices (segmodel_large_specs)")
     x = sub.add_parser("export", help="write weights as the library's network file")
     x.add_argument("--weights", default=WEIGHTS)
     x.add_argument("--out", default=WEIGHTS_BIN)
@@ -379,8 +381,10 @@ def main(argv=None) -> int:
         specs = mg.segmodel_specs(args.count, seed=args.seed)
         cut = int(round(len(specs) * args.train_frac))
         t0 = time.time()
-        X, y, g, totals = seg_collect(specs[:cut], log=lambda s: print(s, flush=True))
-        print(f"collected {len(y)} level rows from {cut} matrices in {time.time() - t0:.1f} s")
+        train = specs[:cut] + (mg.segmodel_large_specs() if args.large else [])
+        X, y, g, totals = seg_collect(train, log=lambda s: print(s, flush=True))
+        print(f"collected {len(y)} level rows from {len(train)} matrices in "
+              f"{time.time() - t0:.1f} s")
         if args.data_out:
             np.savez(args.data_out, X=X, y=y, group=g,
                      totals=np.array([str(t) for t in totals]),
@@ -390,6 +394,9 @@ def main(argv=None) -> int:
         for e, l in hist:
             print(f"epoch {e}: train mse {l:.4f}")
         res = seg_evaluate(m, specs[cut:], log=lambda s: print(s, flush=True))
+        big = seg_evaluate(m, [dict(index=0, family="stencil3d", n=128 ** 3, side=128, nrhs=1,
+                                    seed=2000)], reps=5, log=lambda s: print(s, flush=True))
+        res["stencil3d_128_regret"] = big["geo_regret"]
         res["train_mse_log2"] = float(hist[-1][1])
         print(json.dumps(res))
         m.save(args.out)
