@@ -96,7 +96,8 @@ enum {
 };
 /* SPTRSV_SELECT_SEGMODEL (the matrix-analysis module deciding which levels
  * to rewrite and how deep, Sec. IV): for every kept level t and depth
- * d <= min(max_depth, 8) the segment's features (sptrsv_segment_features)
+ * d <= min(max_depth, 4) (the depths of its training data) the segment's
+ * features (sptrsv_segment_features)
  * go through the process-wide segment network (sptrsv_segmodel_load), whose
  * output is the log2 of the time in microseconds the segment's new level
  * adds to the solve; the segmentation minimising the sum of those times is

@@ -334,6 +334,8 @@ sptrsv_status_t segment_table(sptrsv_plan_t p, int32_t d_max, cudaStream_t s,
     return SPTRSV_OK;
 }
 
+constexpr int32_t kSegMaxDepth = 4;   // deepest segment of the segment network's data
+
 // SELECT_SEGMODEL: the network predicts the log2 time (us) each candidate
 // segment adds to the solve; the segmentation minimising the sum, by
 // dynamic programming over the levels as in SELECT_CRITPATH (ties to the
@@ -474,8 +476,9 @@ sptrsv_status_t choose_segments(sptrsv_plan_t p, cudaStream_t s) {
         }
     } else if (prm.select_mode == SPTRSV_SELECT_SEGMODEL && default_segmodel()) {
         std::vector<std::pair<int32_t, int32_t>> segs;
-        CKS(segmodel_segments(p, default_segmodel(), std::min(std::max(prm.max_depth, 0), 8), s,
-                              &segs));
+        // the network was trained on segments of depth <= kSegMaxDepth
+        CKS(segmodel_segments(p, default_segmodel(),
+                              std::min(std::max(prm.max_depth, 0), kSegMaxDepth), s, &segs));
         for (auto &sg : segs) {
             p->seg_first.push_back(sg.first);
             p->seg_depth.push_back(sg.second);
