@@ -657,6 +657,21 @@ SPTRSV_API sptrsv_status_t sptrsv_critical_path(sptrsv_plan_t p, int32_t hop_wei
 SPTRSV_API sptrsv_status_t sptrsv_codegen_source(sptrsv_plan_t p, int32_t seg, char *buf,
                                                  size_t cap, size_t *len);
 
+/* The same generator on a segment's records given on the host (no plan, no
+ * GPU): nrows rows in solve order grouped into nlev levels, K term slots per
+ * row; h_row[p] the row index x is written to; h_nn[p] the term count (bits
+ * 0-7), the mask of terms read from x (bits 8-23; a segment with any is not
+ * generated) and 1 << 30 for a row whose coefficients are not divided by
+ * its diagonal; h_term[4 (k nrows + p) + 0..3] = (slot q < p of an earlier
+ * row of the segment, 0, low and high 32 bits of the coefficient);
+ * h_diag[2p] = L_ii (used by undivided rows).  Output as for
+ * sptrsv_codegen_source; SPTRSV_ERR_BAD_STATE when the segment would get no
+ * kernel (not thin: 16 or more terms per level on average),
+ * SPTRSV_ERR_INVALID_ARG for a slot that is not an earlier row. */
+SPTRSV_API sptrsv_status_t sptrsv_codegen_source_from_records(
+    int32_t nrows, int32_t K, int32_t nlev, const int32_t *h_row, const int32_t *h_nn,
+    const int32_t *h_term, const double *h_diag, char *buf, size_t cap, size_t *len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -101,6 +101,9 @@ _SIGS = {
     "sptrsv_critical_path": (c_int32, [c_void_p, c_int32, POINTER(c_int64), c_void_p]),
     "sptrsv_codegen_source": (c_int32, [c_void_p, c_int32, c_char_p, c_size_t,
                                         POINTER(c_size_t)]),
+    "sptrsv_codegen_source_from_records": (c_int32, [c_int32, c_int32, c_int32, c_void_p,
+                                                     c_void_p, c_void_p, c_void_p, c_char_p,
+                                                     c_size_t, POINTER(c_size_t)]),
     "sptrsv_level_features": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
     "sptrsv_costmodel_features": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "sptrsv_set_costmodel": (c_int32, [c_void_p, c_void_p]),
@@ -280,6 +283,25 @@ def sptrsv_codegen_source(plan: int, seg: int) -> str:
     buf = create_string_buffer(n.value + 1)
     _check(load().sptrsv_codegen_source(plan, seg, buf, n.value + 1, byref(n)),
            "sptrsv_codegen_source")
+    return buf.value.decode()
+
+
+def sptrsv_codegen_source_from_records(nlev: int, row, nn, term, diag) -> str:
+    """The generator on host records: row, nn int32 [nrows], term int32
+    [K, nrows, 4], diag float64 [nrows, 2] (see the header)."""
+    import numpy as np
+    row = np.ascontiguousarray(row, np.int32)
+    nn = np.ascontiguousarray(nn, np.int32)
+    term = np.ascontiguousarray(term, np.int32)
+    diag = np.ascontiguousarray(diag, np.float64)
+    K, nrows = term.shape[0], term.shape[1]
+    args = (nrows, K, nlev, row.ctypes.data, nn.ctypes.data, term.ctypes.data, diag.ctypes.data)
+    n = c_size_t()
+    _check(load().sptrsv_codegen_source_from_records(*args, None, 0, byref(n)),
+           "sptrsv_codegen_source_from_records")
+    buf = create_string_buffer(n.value + 1)
+    _check(load().sptrsv_codegen_source_from_records(*args, buf, n.value + 1, byref(n)),
+           "sptrsv_codegen_source_from_records")
     return buf.value.decode()
 
 

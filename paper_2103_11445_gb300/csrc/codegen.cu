@@ -106,18 +106,11 @@ bool codegen_eligible(const TailSeg &sg, int32_t max_rows) {
            sg.nrows <= sg.W - sg.T;   // every in-segment term is a window slot
 }
 
-sptrsv_status_t codegen_source(const TailSeg &sg, std::string &src, bool &thin) {
-    const int32_t nr = sg.nrows, K = sg.K;
-    std::vector<int32_t> row(nr), nn(nr);
-    std::vector<int4> term((size_t)K * nr);
-    std::vector<double2> dg(nr);
-    if (cudaMemcpy(row.data(), sg.row.p, sizeof(int32_t) * nr, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(nn.data(), sg.nn.p, sizeof(int32_t) * nr, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(term.data(), sg.term.p, sizeof(int4) * term.size(), cudaMemcpyDeviceToHost) !=
-            cudaSuccess ||
-        cudaMemcpy(dg.data(), sg.diag.p, sizeof(double2) * nr, cudaMemcpyDeviceToHost) !=
-            cudaSuccess)
-        return SPTRSV_ERR_CUDA;
+// The generator proper, on host copies of a segment's records.
+sptrsv_status_t source_from_records(int32_t nr, int32_t K, int32_t nlev, const int32_t *row,
+                                    const int32_t *nn, const int4 *term, const double2 *dg,
+                                    std::string &src, bool &thin) {
+    (void)K;
     int64_t terms = 0;
     for (int32_t p = 0; p < nr; ++p) {
         if ((nn[p] >> 8) & 0xFFFF) {   // a term read from x: not a window slot
@@ -128,7 +121,7 @@ sptrsv_status_t codegen_source(const TailSeg &sg, std::string &src, bool &thin) 
     }
     // one thread pays every FMA in turn: worth it while a level averages
     // fewer than 16 terms (the record-driven kernel's barrier and row cost)
-    thin = terms + nr < 16 * (int64_t)sg.nlev;
+    thin = terms + nr < 16 * (int64_t)nlev;
     if (!thin) return SPTRSV_OK;
     src.clear();
     src.reserve((size_t)(terms * 48 + (int64_t)nr * 96 + 512));
@@ -195,6 +188,23 @@ sptrsv_status_t codegen_source(const TailSeg &sg, std::string &src, bool &thin) 
     return SPTRSV_OK;
 }
 
+
+sptrsv_status_t codegen_source(const TailSeg &sg, std::string &src, bool &thin) {
+    const int32_t nr = sg.nrows, K = sg.K;
+    std::vector<int32_t> row(nr), nn(nr);
+    std::vector<int4> term((size_t)K * nr);
+    std::vector<double2> dg(nr);
+    if (cudaMemcpy(row.data(), sg.row.p, sizeof(int32_t) * nr, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(nn.data(), sg.nn.p, sizeof(int32_t) * nr, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(term.data(), sg.term.p, sizeof(int4) * term.size(), cudaMemcpyDeviceToHost) !=
+            cudaSuccess ||
+        cudaMemcpy(dg.data(), sg.diag.p, sizeof(double2) * nr, cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+        return SPTRSV_ERR_CUDA;
+    return source_from_records(nr, K, sg.nlev, row.data(), nn.data(), term.data(), dg.data(),
+                               src, thin);
+}
+
 sptrsv_status_t codegen_build(TailSeg &sg, double &ms) {
     const auto t0 = std::chrono::steady_clock::now();
     sg.gen.reset();
@@ -249,3 +259,33 @@ cudaError_t codegen_launch(const TailSeg &sg, const double *b, double *x, cudaSt
 }
 
 }  // namespace sptrsv
+
+extern "C" SPTRSV_API sptrsv_status_t sptrsv_codegen_source_from_records(
+    int32_t nrows, int32_t K, int32_t nlev, const int32_t *h_row, const int32_t *h_nn,
+    const int32_t *h_term, const double *h_diag, char *buf, size_t cap, size_t *len) {
+    if (nrows <= 0 || K <= 0 || K > 16 || nlev <= 0 || !h_row || !h_nn || !h_term || !h_diag ||
+        !len)
+        return SPTRSV_ERR_INVALID_ARG;
+    for (int32_t p = 0; p < nrows; ++p) {   // every slot within the segment, counts <= K
+        const int cnt = h_nn[p] & 0xFF;
+        if (cnt > K) return SPTRSV_ERR_INVALID_ARG;
+        for (int k = 0; k < cnt; ++k) {
+            const int32_t q = h_term[4 * ((size_t)k * nrows + p)];
+            if (!((h_nn[p] >> (8 + k)) & 1) && (q < 0 || q >= p)) return SPTRSV_ERR_INVALID_ARG;
+        }
+    }
+    std::string src;
+    bool thin = false;
+    const sptrsv_status_t st = sptrsv::source_from_records(
+        nrows, K, nlev, h_row, h_nn, reinterpret_cast<const int4 *>(h_term),
+        reinterpret_cast<const double2 *>(h_diag), src, thin);
+    if (st != SPTRSV_OK) return st;
+    if (!thin) return SPTRSV_ERR_BAD_STATE;
+    *len = src.size();
+    if (buf && cap > 0) {
+        const size_t k = std::min(cap - 1, src.size());
+        std::memcpy(buf, src.data(), k);
+        buf[k] = 0;
+    }
+    return SPTRSV_OK;
+}

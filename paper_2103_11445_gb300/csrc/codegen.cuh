@@ -17,8 +17,13 @@ TailData tail_view(const TailSeg &t);
 
 // Whether segment sg may get a generated kernel under the caller's limit.
 bool codegen_eligible(const TailSeg &sg, int32_t max_rows);
-// The source of sg's kernel (empty with thin = false when a kernel would not
-// pay: some level is not thin enough, or a term reads x beyond the window).
+// The source of a segment's kernel from host copies of its records (the
+// layout of TailData): empty with thin = false when a kernel would not pay
+// (some level is not thin enough, or a term reads x beyond the window).
+sptrsv_status_t source_from_records(int32_t nr, int32_t K, int32_t nlev, const int32_t *row,
+                                    const int32_t *nn, const int4 *term, const double2 *dg,
+                                    std::string &src, bool &thin);
+// The same for segment sg (its records copied from the device).
 sptrsv_status_t codegen_source(const TailSeg &sg, std::string &src, bool &thin);
 // Generates, compiles and loads sg's kernel into sg.gen (left empty when the
 // segment is not thin); ms accumulates the time taken.  SPTRSV_ERR_CODEGEN
