@@ -25,7 +25,8 @@ Contents (each function cites the passage of the paper it follows):
   the substitutions above, ``pcg.py``;
 * ``features``       per-level features of the matrix-analysis module (rows,
   entries, log2 row-length histogram, ancestor span, fill of each lift;
-  Sec. IV) -- Python, ``features.py``;
+  Sec. IV) and the features of every candidate segment the per-segment cost
+  network reads -- Python, ``features.py``;
 * ``critpath``       weighted critical path of a (transformed) system and
   the critical-path-driven segment selection for synchronisation-free
   solves (Sec. III's remark that rewriting applies to them) -- Python,

@@ -64,3 +64,49 @@ def level_features(A, level: np.ndarray, nlev: int, lifts: int, cap: int) -> np.
                 tot += 2 * (rw.fill - int(_row(A, i)[0].size))
             out[lv, N_BASE + r - 1] = tot
     return out
+
+
+N_SEG = 8
+
+
+def segment_features(A, level: np.ndarray, nlev: int, d_max: int, cap: int):
+    """Features of every candidate segment (kept level t, depth d: levels
+    t..t+d merged, the rows of t+1..t+d rewritten to depend on levels < t),
+    the inputs of the per-segment cost network (this repository's reading,
+    Sec. IV):
+      0 log2(1 + rows), 1 log2(1 + x and b terms), 2 log2(1 + most terms of a
+      row), 3 terms per row, 4 d, 5 fraction of rows rewritten, 6 log2 n,
+      7 log2(nnz / n) (nnz with the diagonal).
+    terms = the kept level's off-diagonal entries plus, per lifted level,
+    its entries and the terms its lift adds; the most terms of a row come
+    from the lift table.  ok[t, d] = False where t + d runs past the last
+    level or a lifted row exceeds the fill cap (and for every deeper d)."""
+    from .critpath import lift_table
+    base = level_features(A, level, nlev, d_max, cap)
+    table = lift_table(A, level, nlev, d_max, cap)
+    nnz = int(A.row_ptr[-1])
+    feat = np.zeros((nlev, d_max + 1, N_SEG))
+    ok = np.zeros((nlev, d_max + 1), dtype=bool)
+    for t in range(nlev):
+        rows = terms = rew = 0.0
+        maxt = 0.0
+        for d in range(d_max + 1):
+            lv = t + d
+            if lv >= nlev:
+                break
+            if d == 0:
+                terms += base[lv, 1]
+                maxt = table[(lv, 0)]
+            else:
+                added = base[lv, N_BASE + d - 1]
+                if added < 0 or table.get((lv, d)) is None:
+                    break
+                terms += base[lv, 1] + added / 2.0
+                maxt = max(maxt, table[(lv, d)])
+                rew += base[lv, 0]
+            rows += base[lv, 0]
+            feat[t, d] = (np.log2(1 + rows), np.log2(1 + terms), np.log2(1 + maxt),
+                          terms / max(rows, 1.0), d, rew / max(rows, 1.0),
+                          np.log2(max(A.n, 1)), np.log2(max(nnz, 1) / max(A.n, 1)))
+            ok[t, d] = True
+    return feat, ok

@@ -69,3 +69,50 @@ def test_lifts_sum_to_the_transform_added_flops():
         for r in range(1, dd + 1):
             tot += f[t + r, 10 + r]
     assert tot == tr.added_flops
+
+
+def test_segment_features_hand_worked_3x3_grid():
+    """Segments of the 3x3 grid worked by hand (nnz = 21 with the diagonal).
+    (0, 1): rows 3, terms 0 + 2 (level 1's entries; lifting it onto level
+    0 trades each x00 term for a b00 term: +0), the longest row 1 term.
+    (0, 2): rows 6; level 2 lifted by 2 adds 6 FLOPs = 3 terms, so terms
+    0 + 2 + 4 + 3 = 9; its longest row is (1,1) with b01, b10, b00."""
+    A = mg.stencil2d(3)
+    lv, nlev = oracle.levels(A)
+    f, ok = fo.segment_features(A, lv, nlev, d_max=2, cap=10**6)
+    ln, ld = np.log2(9), np.log2(21 / 9)
+    np.testing.assert_allclose(f[0, 0], [1, 0, 0, 0, 0, 0, ln, ld])
+    np.testing.assert_allclose(f[0, 1], [2, np.log2(3), 1, 2 / 3, 1, 2 / 3, ln, ld])
+    np.testing.assert_allclose(f[0, 2], [np.log2(7), np.log2(10), 2, 1.5, 2, 5 / 6, ln, ld])
+    assert ok[:3].all() and ok[3].tolist() == [True, True, False]
+    assert ok[4].tolist() == [True, False, False]
+    # a cap of 2 terms rules out lifting level 2 by 2 ((1,1) needs 3)
+    _, ok2 = fo.segment_features(A, lv, nlev, d_max=2, cap=2)
+    assert ok2[0].tolist() == [True, True, False]
+
+
+def test_segment_features_invariants():
+    A = mg.random_lower(60, seed=3, density=0.08)
+    lv, nlev = oracle.levels(A)
+    f, ok = fo.segment_features(A, lv, nlev, d_max=3, cap=10**6)
+    base = fo.level_features(A, lv, nlev, 3, 10**6)
+    rows = np.exp2(f[..., 0]) - 1
+    terms = np.exp2(f[..., 1]) - 1
+    # d = 0: the level itself
+    np.testing.assert_allclose(rows[:, 0], base[:, 0])
+    np.testing.assert_allclose(terms[:, 0], base[:, 1])
+    assert (f[:, :, 4][ok] == np.broadcast_to(np.arange(4), ok.shape)[ok]).all()
+    # merging never loses a row or a term, and rewrites at least the lifted rows
+    for t in range(nlev):
+        for d in range(1, 4):
+            if ok[t, d]:
+                assert np.isclose(rows[t, d], rows[t, d - 1] + base[t + d, 0])
+                assert terms[t, d] >= terms[t, d - 1] + base[t + d, 1] - 1e-9
+                assert f[t, d, 5] > 0
+    # a segmentation into feasible segments covers every row once
+    t, total = 0, 0.0
+    while t < nlev:
+        d = max(k for k in range(4) if ok[t, k])
+        total += rows[t, d]
+        t += d + 1
+    assert np.isclose(total, A.n)
